@@ -1,0 +1,419 @@
+#!/usr/bin/env python3
+"""Benchmark: SurfaceNets extract + constrained smoothing throughput on one GB300.
+
+One step = sn_extract of one label map resident in HBM (including the count
+read-back that sizes the outputs) + sn_smooth (16 Jacobi sweeps) + sn_free.
+Default workload: the 512^3 uint16 atlas-like map with 93 labels (stand-in for
+the paper's segmented Torso/atlas data), 16 iterations, relaxation 0.5,
+constraint 1 voxel.  The map (268 MB) is larger than L2, so no flush is needed
+between steps.
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank processes its own copy
+of the map (independent units, weak scaling, no collective on the data path);
+value = voxels of all ranks / max time over ranks.
+
+--impl reference times the FP64 sequential oracle on the host cores on a
+bounded slab of the same map (the CPU baseline arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "extract+smooth Gvoxels/s & HBM roofline frac; learned vs plain at ≤1e-3 vox"
+UNIT = "Gvoxels/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "synthetic"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-slab", type=int, default=0, help="z-slices of the map the oracle baseline runs on")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def make_workload(name):
+    import sn_synth
+    if name == "c1":
+        return sn_synth.config1()
+    if name == "c2":
+        return sn_synth.config2()
+    if name == "c3":
+        return sn_synth.config3()
+    return sn_synth.paper_synthetic()
+
+
+def workload_config(w, extra=None):
+    cfg = {"workload": w.name, "dims": list(w.dims), "label_dtype": str(w.labels.dtype),
+           "labels": int(len(np.unique(w.labels)) - (1 if (w.labels == w.background).any() else 0)),
+           "iterations": w.iterations, "relaxation": w.relaxation, "constraint_voxels": w.constraint,
+           "spacing": list(w.spacing),
+           "l2": "inputs larger than L2 (%.0f MB label map), no flush" % (w.labels.nbytes / 1e6),
+           "map_sha256": hashlib.sha256(w.labels.tobytes()).hexdigest()[:16]}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------- roofline inputs
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes(V, b, P, Q, S, n):
+    """Bytes the method must move: read labels once, write the mesh once, and
+    read + write every offset float3 once per Jacobi sweep."""
+    return {"labels": V * b, "mesh": 12 * P + (16 + 2 * b) * Q + 8 * (P + 1) + 4 * S, "smooth": 24 * n * P}
+
+
+def kernel_units(name, V, b, P, Q, S, n):
+    """(algorithmic bytes per launch, unit description) for each kernel."""
+    if name == "k_smooth":
+        return 24 * P, "24 B per point (read+write one float3 offset)"
+    if name == "k_planes":
+        return V * b, "%d B per voxel (labels read once)" % b
+    if name == "k_emit":
+        return 12 * P + (16 + 2 * b) * Q + 8 * (P + 1) + 4 * S, "mesh bytes written once"
+    return None, None
+
+
+def traffic_for(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary, if it matches the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        ent = d.get(kernel)
+        if not ent:
+            return None
+        src = os.path.join(ROOT, ent["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if sha != ent["source_sha256"]:
+            return None
+        return ent["dram_bytes_per_launch_full"]
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- reference
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    w = make_workload(args.workload)
+    nz = w.labels.shape[0]
+    slab = args.cpu_slab or max(2, min(nz, 16))
+    z0 = max(0, nz // 2 - slab // 2)
+    lab = np.ascontiguousarray(w.labels[z0:z0 + slab])
+    V = lab.size
+
+    def once():
+        t = time.perf_counter()
+        m = oracle.extract(lab, w.spacing, w.origin, background=w.background)
+        oracle.smooth(m, w.spacing, w.origin, w.iterations, w.relaxation, w.constraint)
+        return time.perf_counter() - t
+
+    for _ in range(args.warmup):
+        once()
+    ts = [once() for _ in range(args.steps)]
+    tot = sum(ts)
+    value = V * args.steps / tot / 1e9
+    sample = "slices z=[%d,%d) of the map (%dx%dx%d voxels) per step, extract + %d sweeps" % (
+        z0, z0 + slab, lab.shape[2], lab.shape[1], lab.shape[0], w.iterations)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, {"sample": sample}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline(w, seconds_target=12.0):
+    """Oracle extract + smooth on a bounded slab of the map, 1 host core."""
+    import oracle
+    nz = w.labels.shape[0]
+    slab = max(2, min(nz, 8))
+    z0 = max(0, nz // 2 - slab // 2)
+    lab = np.ascontiguousarray(w.labels[z0:z0 + slab])
+    t = time.perf_counter()
+    m = oracle.extract(lab, w.spacing, w.origin, background=w.background)
+    oracle.smooth(m, w.spacing, w.origin, w.iterations, w.relaxation, w.constraint)
+    dt = time.perf_counter() - t
+    # grow the slab to roughly seconds_target of CPU work
+    if dt < seconds_target / 4 and slab < nz:
+        slab = int(min(nz, max(slab + 1, slab * seconds_target / max(dt, 1e-3))))
+        z0 = max(0, nz // 2 - slab // 2)
+        lab = np.ascontiguousarray(w.labels[z0:z0 + slab])
+        t = time.perf_counter()
+        m = oracle.extract(lab, w.spacing, w.origin, background=w.background)
+        oracle.smooth(m, w.spacing, w.origin, w.iterations, w.relaxation, w.constraint)
+        dt = time.perf_counter() - t
+    sample = "slices z=[%d,%d) of the map (%d voxels), extract + %d sweeps, one run" % (
+        z0, z0 + slab, lab.size, w.iterations)
+    return {"value": lab.size / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "seconds": dt}
+
+
+# --------------------------------------------------------------------- ours
+def to_device(labels):
+    import torch
+    isz = labels.dtype.itemsize
+    t = torch.from_numpy(np.ascontiguousarray(labels).view({1: np.uint8, 2: np.int16, 4: np.int32}[isz]))
+    return t.cuda().view({1: torch.uint8, 2: torch.uint16, 4: torch.uint32}[isz])
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2401_14906_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2401_14906_gb300 import sn
+    sn.load()
+
+    w = make_workload(args.workload)
+    V, b = w.voxels, w.labels.dtype.itemsize
+    lab_dev = to_device(w.labels)
+    stream = torch.cuda.Stream()
+
+    def step():
+        m = sn.sn_extract(lab_dev, w.spacing, w.origin, background=w.background, stream=stream)
+        sn.sn_smooth(m, w.iterations, w.relaxation, w.constraint)
+        cnt = m.counts
+        m.free()
+        return cnt
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            counts = step()
+        torch.cuda.synchronize()
+        P, Q, S = counts
+
+        def barrier():
+            if world > 1:
+                dist.barrier()
+
+        sampler = ClockSampler(torch.cuda.current_device())
+        sampler.start()
+        time.sleep(0.3)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        ms_step = ms / args.steps
+        value = world * V * args.steps / (ms / 1e3) / 1e9
+
+        # per-kernel durations: the same steps again with events around every launch
+        sn.sn_profile_read(reset=True)
+        sn.sn_profile_enable(True)
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize()
+        prof = sn.sn_profile_read(reset=True)
+        sn.sn_profile_enable(False)
+
+        # end to end through the C ABI with host buffers: pinned labels in, full mesh out
+        e2e = None
+        if not args.no_e2e:
+            host_lab = torch.empty(w.labels.size * b, dtype=torch.uint8, pin_memory=True)
+            host_lab.numpy()[:] = np.ascontiguousarray(w.labels).view(np.uint8).ravel()
+            out_bufs = {k: torch.empty(n, dtype=torch.uint8, pin_memory=True) for k, n in
+                        [("points", 12 * P), ("quads", 16 * Q), ("quad_labels", 2 * b * Q),
+                         ("stencil_offsets", 8 * (P + 1)), ("stencil_ids", 4 * S)]}
+            d2h = sum(t.numel() for t in out_bufs.values())
+            lib = sn.load()
+            import ctypes
+
+            def e2e_step():
+                d = (ctypes.c_int64 * 3)(*w.dims)
+                sp = (ctypes.c_double * 3)(*w.spacing)
+                org = (ctypes.c_double * 3)(*w.origin)
+                out = ctypes.c_void_p()
+                rc = lib.sn_extract(ctypes.c_void_p(host_lab.data_ptr()), b, d, sp, org, None, 0, w.background,
+                                    ctypes.c_void_p(stream.cuda_stream), ctypes.byref(out))
+                assert rc == 0, sn.sn_last_error()
+                rc = lib.sn_smooth(out, w.iterations, w.relaxation, w.constraint)
+                assert rc == 0
+                rc = lib.sn_mesh_copy_to_host(out, ctypes.c_void_p(out_bufs["points"].data_ptr()),
+                                              ctypes.c_void_p(out_bufs["quads"].data_ptr()),
+                                              ctypes.c_void_p(out_bufs["quad_labels"].data_ptr()),
+                                              ctypes.c_void_p(out_bufs["stencil_offsets"].data_ptr()),
+                                              ctypes.c_void_p(out_bufs["stencil_ids"].data_ptr()), None)
+                assert rc == 0
+                lib.sn_free(out)
+
+            for _ in range(2):
+                e2e_step()
+            torch.cuda.synchronize()
+            barrier()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(args.steps):
+                e2e_step()
+            z.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            ems = a.elapsed_time(z)
+            if world > 1:
+                t = torch.tensor([ems], device="cuda")
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                ems = float(t.item())
+            e2e = {"value": world * V * args.steps / (ems / 1e3) / 1e9, "unit": UNIT,
+                   "h2d_bytes_per_step": V * b, "d2h_bytes_per_step": int(d2h),
+                   "ms_per_step": ems / args.steps}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = peaks()
+    alg = algorithmic_bytes(V, b, P, Q, S, w.iterations)
+    alg_total = sum(alg.values())
+    kernels = {}
+    launches_per_step = 0
+    for name, (n, tot) in prof.items():
+        per_step = n / args.steps
+        launches_per_step += per_step
+        kernels[name] = {"launches_per_step": per_step, "ms_per_step": tot / args.steps,
+                         "ms_per_launch": tot / max(n, 1)}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"]) if kernels else None
+    roof = None
+    if dom:
+        by, unit_desc = kernel_units(dom, V, b, P, Q, S, w.iterations)
+        if by is not None:
+            ach = by / (kernels[dom]["ms_per_launch"] / 1e3) / 1e9
+            roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "peak_kind": peak_kind + " (burst copy)", "traffic": traffic_for(dom),
+                    "algorithmic_bytes_per_launch": by, "unit_bytes": unit_desc}
+    path_time = ms_step / 1e3
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u%d+f32" % (8 * b), "data": "synthetic",
+            "config": workload_config(w, {"parallelism": "replicas" if world > 1 else "single",
+                                          "points": P, "quads": Q, "stencil_entries": S}),
+            "roofline": roof,
+            "path_roofline": {"algorithmic_bytes_per_step": alg_total, "bytes_breakdown": alg,
+                              "achieved_gbs": alg_total / path_time / 1e9, "peak": peak,
+                              "frac": alg_total / path_time / 1e9 / peak},
+            "kernels": kernels, "gpu_launches": int(round(launches_per_step * args.steps)),
+            "clocks": clocks, "e2e": e2e}
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(w)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

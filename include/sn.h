@@ -1,0 +1,158 @@
+/*
+ * sn.h -- C ABI of the GB300 SurfaceNets library (libsn.so).
+ *
+ * The library extracts one shared quad mesh from a 3-D segmentation label map
+ * and smooths it, following "A High-Performance SurfaceNets Discrete
+ * Isocontouring Algorithm" (arXiv 2401.14906):
+ *
+ *   sn_extract  Sec. 2.2-2.3: every voxel cell with an intersected edge gets a
+ *               point at its centre, every intersected edge gets a quad joining
+ *               the four cells that share it, each quad carries the two labels it
+ *               separates, and every point gets a face-neighbour smoothing
+ *               stencil (the face case of Sec. 3.3).
+ *   sn_smooth   Sec. 2.2 Eq. 1 with the double buffer of Sec. 2.4: points move
+ *               towards the mean of their stencil neighbours, clamped to a box
+ *               around their generating cell; it always restarts from the cached
+ *               extraction (the smoothing cache of Sec. 3.7).
+ *
+ * Conventions fixed by this library where the paper is silent:
+ *   - label maps are x-fastest: sample (i,j,k) is element i + nx*(j + ny*k);
+ *   - voxel cells span samples c..c+1 with c in [-1, n-1] per axis (the
+ *     one-voxel padding of Sec. 3.2), so regions touching the volume faces get
+ *     points half a voxel outside the volume and stay open (Sec. 4.2);
+ *   - points are numbered in (cz, cy, cx) order of their cells; quads in
+ *     (k, j, i) order of the first sample of their edge, then axis x, y, z
+ *     (the row-major prefix-sum order of Sec. 2.3, Pass 3);
+ *   - a quad lists its cells counter-clockwise seen from +axis (normal along the
+ *     edge, from s0 to s1) and carries (class(s0), class(s1));
+ *   - stencil neighbours are listed in face order -x, +x, -y, +y, -z, +z;
+ *   - the constraint box of a point is its cell centre +- d/2 voxel per axis.
+ *
+ * All device work runs on the CUDA stream given to sn_extract, in order with
+ * the caller's other work on that stream.  The library is thread-safe for
+ * distinct meshes; one mesh must not be used from two threads at once.
+ */
+#ifndef SN_H
+#define SN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SN_OK = 0,
+    SN_EINVAL = 1,    /* an argument is out of range or NULL where it may not be */
+    SN_ENOMEM = 2,    /* a device or host allocation failed */
+    SN_EOVERFLOW = 3, /* more than INT32_MAX points (point ids are int32) */
+    SN_ECUDA = 4,     /* a CUDA runtime call failed; sn_last_error() has the detail */
+    SN_ETIMEOUT = 5   /* a bounded device-side wait gave up (the scan look-back) */
+} sn_status;
+
+typedef enum { SN_U8 = 1, SN_U16 = 2, SN_U32 = 4 } sn_label_type; /* value = bytes per label */
+
+typedef struct sn_mesh sn_mesh; /* opaque, owned by the library until sn_free */
+
+/*
+ * sn_extract -- surface extraction (Sec. 2.2, Sec. 2.3 Passes 1-4).
+ *
+ * labels      label map, dims[0]*dims[1]*dims[2] values of `type`, x fastest.
+ *             May be device memory (read in place) or host memory (copied to
+ *             the device on `cuda_stream` first).  Caller-owned, read-only, and
+ *             must stay valid until sn_extract returns.
+ * type        SN_U8, SN_U16 or SN_U32.
+ * dims        (nx, ny, nz), each >= 1 and <= 2^21 - 2; nx*ny*nz < 2^40.
+ * spacing     voxel size per axis (finite, > 0); origin: world position of
+ *             sample (0,0,0) (finite).  Point coordinates are
+ *             origin + spacing * (c + 1/2 + offset), rounded once to float.
+ * selected    the label set L of Sec. 2.1: the labels to extract.  Every value
+ *             not in L is background.  NULL with n_selected == 0 selects every
+ *             value other than `background`.  Values must fit the label type,
+ *             be distinct from `background`; duplicates are allowed.
+ *             Caller-owned host memory, read during the call only.
+ * background  the value reported for the background class in quad labels.
+ * cuda_stream a cudaStream_t (NULL = the legacy default stream).
+ * out         receives the new mesh; set to NULL on failure.
+ *
+ * Returns after the kernels are enqueued and the output sizes are known (the
+ * call waits for the counting passes on `cuda_stream`).  An empty result (no
+ * point) is SN_OK.  Errors: SN_EINVAL, SN_ENOMEM, SN_EOVERFLOW, SN_ECUDA,
+ * SN_ETIMEOUT.  The device arrays start as the unsmoothed mesh: points at the
+ * cell centres and offsets 0.
+ */
+sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[3], const double spacing[3],
+                     const double origin[3], const uint32_t *selected, int64_t n_selected, uint32_t background,
+                     void *cuda_stream, sn_mesh **out);
+
+/*
+ * sn_smooth -- constrained Laplacian smoothing (Sec. 2.2 Eq. 1, Sec. 2.4).
+ *
+ * Restarts from the cell centres, then runs `iterations` Jacobi sweeps:
+ *   o_i <- clamp(o_i + relaxation * mean_j (p_j - p_i), -d/2, +d/2) per axis,
+ * every sweep reading only the previous sweep's positions (double buffer).
+ * iterations >= 0; relaxation finite and >= 0; constraint_distance d finite
+ * and >= 0 (d = 1 keeps each point inside its voxel cell).  Afterwards the
+ * mesh's `points` hold the smoothed world positions and `offsets` the
+ * displacement from the cell centre in voxel units.  Enqueued on the mesh's
+ * stream; returns without waiting.  Errors: SN_EINVAL, SN_ENOMEM, SN_ECUDA.
+ */
+sn_status sn_smooth(sn_mesh *m, int iterations, float relaxation, float constraint_distance);
+
+/* Output sizes: points, quads, stencil entries (sum of stencil lengths). */
+sn_status sn_mesh_counts(const sn_mesh *m, int64_t *n_points, int64_t *n_quads, int64_t *n_stencil);
+
+/*
+ * Borrowed device pointers into the mesh, valid until sn_free; any may be NULL
+ * to skip it.  Layouts:
+ *   points          float [n_points][3]  world coordinates
+ *   quads           int32 [n_quads][4]   point ids
+ *   quad_labels     label type [n_quads][2]  (class(s0), class(s1))
+ *   stencil_offsets int64 [n_points + 1] CSR row starts into stencil_ids
+ *   stencil_ids     int32 [n_stencil]    face-neighbour point ids
+ *   offsets         float [n_points][3]  displacement from the cell centre, voxels
+ */
+sn_status sn_mesh_device_arrays(const sn_mesh *m, const float **points, const int32_t **quads,
+                                const void **quad_labels, const int64_t **stencil_offsets,
+                                const int32_t **stencil_ids, const float **offsets);
+
+/* Borrowed device pointer to the 6-bit face case of each point (uint8
+ * [n_points], bit f set iff face f in -x,+x,-y,+y,-z,+z is in the stencil,
+ * Sec. 3.3). */
+sn_status sn_mesh_face_masks(const sn_mesh *m, const uint8_t **face_masks);
+
+/* Copies the arrays above into caller-allocated host buffers (any may be NULL)
+ * with the layouts of sn_mesh_device_arrays; waits for the mesh's stream. */
+sn_status sn_mesh_copy_to_host(const sn_mesh *m, float *points, int32_t *quads, void *quad_labels,
+                               int64_t *stencil_offsets, int32_t *stencil_ids, float *offsets);
+
+/* Releases the mesh and its device memory (stream-ordered).  NULL is a no-op. */
+void sn_free(sn_mesh *m);
+
+/* Static description of a status code. */
+const char *sn_status_string(sn_status s);
+
+/* Detail of the last failure on the calling thread ("" if none). */
+const char *sn_last_error(void);
+
+/*
+ * Kernel timing for roofline reports.  While enabled, every library kernel
+ * launch is bracketed by CUDA events on its launch stream, and the per-kernel
+ * totals accumulate until read.  Off by default (it adds event records between
+ * launches).  sn_profile_read fills up to `cap` entries and returns the number
+ * of kernels seen; names are static strings.
+ */
+typedef struct {
+    const char *name;
+    int64_t launches;
+    double total_ms; /* sum of event-measured durations */
+} sn_kernel_time;
+
+void sn_profile_enable(int on);
+int sn_profile_read(sn_kernel_time *out, int cap, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SN_H */

@@ -1,0 +1,495 @@
+// sn_api.cu -- host side of the C ABI declared in include/sn.h: argument
+// checks, device memory (a library-owned stream-ordered pool), the launch
+// sequence of one extraction, the count read-back, and kernel timing.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sn_internal.h"
+
+struct sn_mesh {
+    int device;
+    cudaStream_t stream;
+    sn_label_type type;
+    int64_t dims[3];
+    double spacing[3];
+    double origin[3];
+    int64_t np, nq, ns;
+    sn::MeshArrays a;
+    float *smooth_scratch;
+    cudaMemPool_t pool;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sn_status fail(sn_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+sn_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(SN_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------- memory pool
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
+cudaError_t device_pool(int dev, cudaMemPool_t *out)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    cudaError_t e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX; // keep freed blocks for reuse instead of returning them at every sync
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) return e;
+    g_pools[dev] = pool;
+    *out = pool;
+    return cudaSuccess;
+}
+
+// Stream-ordered allocation of at least 256 bytes (so that empty arrays still
+// get a valid pointer).
+sn_status pool_alloc(void **p, size_t bytes, cudaMemPool_t pool, cudaStream_t st, const char *what)
+{
+    *p = nullptr;
+    size_t n = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMallocFromPoolAsync(p, n, pool, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(SN_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) + " bytes for " + what +
+                                   " failed: " + cudaGetErrorString(e));
+    }
+    return SN_OK;
+}
+
+void pool_free(void *p, cudaStream_t st)
+{
+    if (p) cudaFreeAsync(p, st);
+}
+
+// Pinned host block for the count read-back, one per thread.
+sn::DevTotals *host_totals()
+{
+    thread_local sn::DevTotals *h = nullptr;
+    if (!h) {
+        if (cudaMallocHost((void **)&h, sizeof(sn::DevTotals)) != cudaSuccess) {
+            cudaGetLastError();
+            h = nullptr;
+        }
+    }
+    return h;
+}
+
+// ---------------------------------------------------------------- profiling
+std::atomic<int> g_prof_on{0};
+std::mutex g_prof_mu;
+struct ProfEntry {
+    int64_t launches = 0;
+    double total_ms = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+std::map<std::string, ProfEntry> g_prof;
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+} // namespace
+
+namespace sn {
+
+ProfScope::ProfScope(const char *name, cudaStream_t st) : name_(name), st_(st), a_(nullptr), b_(nullptr), on_(false)
+{
+    if (!g_prof_on.load()) return;
+    if (cudaEventCreate(&a_) != cudaSuccess || cudaEventCreate(&b_) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    on_ = cudaEventRecord(a_, st_) == cudaSuccess;
+}
+
+ProfScope::~ProfScope()
+{
+    if (!on_) {
+        if (a_) cudaEventDestroy(a_);
+        if (b_) cudaEventDestroy(b_);
+        return;
+    }
+    cudaEventRecord(b_, st_);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfEntry &e = g_prof[name_];
+    e.launches++;
+    e.pending.emplace_back(a_, b_);
+}
+
+} // namespace sn
+
+extern "C" {
+
+void sn_profile_enable(int on) { g_prof_on.store(on ? 1 : 0); }
+
+int sn_profile_read(sn_kernel_time *out, int cap, int reset)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int n = 0;
+    for (auto &kv : g_prof) {
+        ProfEntry &e = kv.second;
+        for (auto &pr : e.pending) {
+            float ms = 0.f;
+            cudaEventSynchronize(pr.second);
+            if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) e.total_ms += ms;
+            cudaGetLastError();
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        e.pending.clear();
+        if (out && n < cap) {
+            // names are the string literals passed to ProfScope: static storage
+            out[n].name = kv.first.c_str();
+            out[n].launches = e.launches;
+            out[n].total_ms = e.total_ms;
+        }
+        ++n;
+    }
+    if (reset) {
+        for (auto &kv : g_prof) {
+            kv.second.launches = 0;
+            kv.second.total_ms = 0.0;
+        }
+    }
+    return n;
+}
+
+const char *sn_status_string(sn_status s)
+{
+    switch (s) {
+    case SN_OK: return "SN_OK: success";
+    case SN_EINVAL: return "SN_EINVAL: invalid argument";
+    case SN_ENOMEM: return "SN_ENOMEM: out of memory";
+    case SN_EOVERFLOW: return "SN_EOVERFLOW: more than INT32_MAX points";
+    case SN_ECUDA: return "SN_ECUDA: CUDA runtime error";
+    case SN_ETIMEOUT: return "SN_ETIMEOUT: device-side wait limit reached";
+    }
+    return "unknown sn_status";
+}
+
+const char *sn_last_error(void) { return g_last_error.c_str(); }
+
+sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[3], const double spacing[3],
+                     const double origin[3], const uint32_t *selected, int64_t n_selected, uint32_t background,
+                     void *cuda_stream, sn_mesh **out)
+{
+    g_last_error.clear();
+    if (!out) return fail(SN_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!labels) return fail(SN_EINVAL, "labels is NULL");
+    if (type != SN_U8 && type != SN_U16 && type != SN_U32) return fail(SN_EINVAL, "bad label type");
+    if (!dims || !spacing || !origin) return fail(SN_EINVAL, "dims, spacing or origin is NULL");
+    const int64_t kMaxDim = (1ll << 21) - 2;
+    for (int a = 0; a < 3; ++a) {
+        if (dims[a] < 1 || dims[a] > kMaxDim) return fail(SN_EINVAL, "dims must be in [1, 2^21-2]");
+        if (!finite_pos(spacing[a])) return fail(SN_EINVAL, "spacing must be finite and > 0");
+        if (!std::isfinite(origin[a])) return fail(SN_EINVAL, "origin must be finite");
+    }
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+    const int64_t V = nx * ny * nz;
+    if (V >= (1ll << 40)) return fail(SN_EINVAL, "nx*ny*nz must be < 2^40");
+    const uint64_t tmax = type == SN_U8 ? 0xffull : type == SN_U16 ? 0xffffull : 0xffffffffull;
+    if ((uint64_t)background > tmax) return fail(SN_EINVAL, "background does not fit the label type");
+    if (n_selected < 0 || (n_selected > 0 && !selected) || (selected && n_selected == 0))
+        return fail(SN_EINVAL, "selected/n_selected mismatch");
+    std::vector<uint32_t> sel;
+    if (selected) {
+        sel.assign(selected, selected + n_selected);
+        for (uint32_t v : sel) {
+            if ((uint64_t)v > tmax) return fail(SN_EINVAL, "a selected label does not fit the label type");
+            if (v == background) return fail(SN_EINVAL, "a selected label equals the background value");
+        }
+        std::sort(sel.begin(), sel.end());
+        sel.erase(std::unique(sel.begin(), sel.end()), sel.end());
+    }
+
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    cudaMemPool_t pool;
+    e = device_pool(dev, &pool);
+    if (e != cudaSuccess) return cuda_fail(e, "memory pool");
+    sn::DevTotals *htot = host_totals();
+    if (!htot) return fail(SN_ENOMEM, "pinned host allocation failed");
+
+    std::vector<void *> temps; // freed (stream-ordered) on every exit path
+    auto cleanup = [&]() {
+        for (void *p : temps) pool_free(p, st);
+        temps.clear();
+    };
+    auto talloc = [&](void **p, size_t bytes, const char *what) -> sn_status {
+        sn_status r = pool_alloc(p, bytes, pool, st, what);
+        if (r == SN_OK) temps.push_back(*p);
+        return r;
+    };
+
+    // labels: in place when the device can read them, else one copy
+    const size_t lab_bytes = (size_t)V * (size_t)type;
+    const void *dlabels = labels;
+    cudaPointerAttributes attr;
+    e = cudaPointerGetAttributes(&attr, labels);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        attr.type = cudaMemoryTypeUnregistered;
+    }
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
+        void *d = nullptr;
+        sn_status r = talloc(&d, lab_bytes, "label copy");
+        if (r != SN_OK) return cleanup(), r;
+        e = cudaMemcpyAsync(d, labels, lab_bytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cleanup(), cuda_fail(e, "label copy");
+        dlabels = d;
+    }
+
+    // classifier (Sec. 3.1)
+    sn::Classifier cls;
+    std::memset(&cls, 0, sizeof(cls));
+    cls.background = background;
+    cls.mode = sn::CLASS_ALL;
+    if (selected) {
+        const uint32_t vmax = sel.empty() ? 0u : sel.back();
+        if (vmax < (1u << 24)) {
+            cls.mode = sn::CLASS_BITMAP;
+            cls.nbits = vmax + 1u;
+            std::vector<uint32_t> bm((cls.nbits + 31) / 32, 0u);
+            for (uint32_t v : sel) bm[v >> 5] |= 1u << (v & 31u);
+            void *d = nullptr;
+            sn_status r = talloc(&d, bm.size() * 4, "label bitmap");
+            if (r != SN_OK) return cleanup(), r;
+            e = cudaMemcpyAsync(d, bm.data(), bm.size() * 4, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st); // bm is a local vector
+            if (e != cudaSuccess) return cleanup(), cuda_fail(e, "label bitmap copy");
+            cls.bitmap = (const uint32_t *)d;
+        } else {
+            cls.mode = sn::CLASS_SORTED;
+            cls.nsorted = (int64_t)sel.size();
+            void *d = nullptr;
+            sn_status r = talloc(&d, sel.size() * 4, "label list");
+            if (r != SN_OK) return cleanup(), r;
+            e = cudaMemcpyAsync(d, sel.data(), sel.size() * 4, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cleanup(), cuda_fail(e, "label list copy");
+            cls.sorted = (const uint32_t *)d;
+        }
+    }
+
+    sn::Geometry g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.W = (nx + 1 + 31) / 32;
+    g.Rs = ny * nz;
+    g.Rc = (ny + 1) * (nz + 1);
+    const int ntiles = (int)((g.Rc + sn::kScanTile - 1) / sn::kScanTile);
+
+    sn::ExtractScratch s;
+    std::memset(&s, 0, sizeof(s));
+    struct {
+        void **p;
+        size_t bytes;
+        const char *what;
+    } plan[] = {
+        {(void **)&s.X, sizeof(uint32_t) * (size_t)(g.Rs * g.W), "X plane"},
+        {(void **)&s.Y, sizeof(uint32_t) * (size_t)(g.Rs * g.W), "Y plane"},
+        {(void **)&s.Z, sizeof(uint32_t) * (size_t)(g.Rs * g.W), "Z plane"},
+        {(void **)&s.P, sizeof(uint32_t) * (size_t)(g.Rc * g.W), "point plane"},
+        {(void **)&s.preP, sizeof(int32_t) * (size_t)(g.Rc * g.W), "point rank plane"},
+        {(void **)&s.cntP, sizeof(int32_t) * (size_t)g.Rc, "point counts"},
+        {(void **)&s.cntS, sizeof(int32_t) * (size_t)g.Rc, "stencil counts"},
+        {(void **)&s.cntQ, sizeof(int32_t) * (size_t)g.Rc, "quad counts"},
+        {(void **)&s.offP, sizeof(int64_t) * (size_t)(g.Rc + 1), "point offsets"},
+        {(void **)&s.offS, sizeof(int64_t) * (size_t)(g.Rc + 1), "stencil offsets"},
+        {(void **)&s.offQ, sizeof(int64_t) * (size_t)(g.Rc + 1), "quad offsets"},
+        {(void **)&s.scan_flags, sizeof(int32_t) * (size_t)ntiles, "scan flags"},
+        {(void **)&s.scan_vals, sizeof(int64_t) * 6 * (size_t)ntiles, "scan values"},
+        {(void **)&s.scan_ticket, sizeof(uint32_t), "scan ticket"},
+    };
+    for (auto &pl : plan) {
+        sn_status r = talloc(pl.p, pl.bytes, pl.what);
+        if (r != SN_OK) return cleanup(), r;
+    }
+    sn::DevTotals *dtot = nullptr;
+    {
+        sn_status r = talloc((void **)&dtot, sizeof(sn::DevTotals), "totals");
+        if (r != SN_OK) return cleanup(), r;
+    }
+
+    // Passes 1-3
+    if ((e = sn::launch_planes(type, dlabels, cls, g, s, st)) != cudaSuccess)
+        return cleanup(), cuda_fail(e, "k_planes launch");
+    if ((e = sn::launch_cellrows(g, s, st)) != cudaSuccess) return cleanup(), cuda_fail(e, "k_cellrows launch");
+    if ((e = sn::launch_scan(g, s, dtot, st)) != cudaSuccess) return cleanup(), cuda_fail(e, "k_scan launch");
+    e = cudaMemcpyAsync(htot, dtot, sizeof(sn::DevTotals), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cleanup(), cuda_fail(e, "count read-back");
+    if (htot->error) return cleanup(), fail(SN_ETIMEOUT, "row scan look-back wait limit reached");
+    const int64_t np = htot->n_points, nq = htot->n_quads, ns = htot->n_stencil;
+    if (np > (int64_t)INT32_MAX) return cleanup(), fail(SN_EOVERFLOW, "more than INT32_MAX points");
+
+    // exact allocation of the outputs (end of Pass 3)
+    sn_mesh *m = (sn_mesh *)std::calloc(1, sizeof(sn_mesh));
+    if (!m) return cleanup(), fail(SN_ENOMEM, "host allocation failed");
+    m->device = dev;
+    m->stream = st;
+    m->type = type;
+    m->pool = pool;
+    for (int a = 0; a < 3; ++a) {
+        m->dims[a] = dims[a];
+        m->spacing[a] = spacing[a];
+        m->origin[a] = origin[a];
+    }
+    m->np = np;
+    m->nq = nq;
+    m->ns = ns;
+    struct {
+        void **p;
+        size_t bytes;
+        const char *what;
+    } oplan[] = {
+        {(void **)&m->a.points, sizeof(float) * 3 * (size_t)np, "points"},
+        {(void **)&m->a.offsets, sizeof(float) * 3 * (size_t)np, "offsets"},
+        {(void **)&m->a.cells, sizeof(uint64_t) * (size_t)np, "cells"},
+        {(void **)&m->a.quads, sizeof(int32_t) * 4 * (size_t)nq, "quads"},
+        {(void **)&m->a.quad_labels, (size_t)type * 2 * (size_t)nq, "quad labels"},
+        {(void **)&m->a.sten_off, sizeof(int64_t) * (size_t)(np + 1), "stencil offsets"},
+        {(void **)&m->a.sten_ids, sizeof(int32_t) * (size_t)ns, "stencil ids"},
+        {(void **)&m->a.face_mask, (size_t)np, "face masks"},
+    };
+    for (auto &pl : oplan) {
+        sn_status r = pool_alloc(pl.p, pl.bytes, pool, st, pl.what);
+        if (r != SN_OK) {
+            sn_free(m);
+            return cleanup(), r;
+        }
+    }
+
+    // Pass 4
+    if ((e = sn::launch_emit(type, dlabels, cls, g, s, m->a, spacing, origin, dtot, st)) != cudaSuccess) {
+        sn_free(m);
+        return cleanup(), cuda_fail(e, "k_emit launch");
+    }
+    e = cudaMemcpyAsync(m->a.sten_off + np, s.offS + g.Rc, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) {
+        sn_free(m);
+        return cleanup(), cuda_fail(e, "stencil offset tail");
+    }
+    cleanup();
+    *out = m;
+    return SN_OK;
+}
+
+sn_status sn_smooth(sn_mesh *m, int iterations, float relaxation, float constraint_distance)
+{
+    g_last_error.clear();
+    if (!m) return fail(SN_EINVAL, "mesh is NULL");
+    if (iterations < 0) return fail(SN_EINVAL, "iterations must be >= 0");
+    if (!std::isfinite(relaxation) || relaxation < 0.f) return fail(SN_EINVAL, "relaxation must be finite and >= 0");
+    if (!std::isfinite(constraint_distance) || constraint_distance < 0.f)
+        return fail(SN_EINVAL, "constraint distance must be finite and >= 0");
+    if (m->np == 0) return SN_OK;
+    if (iterations > 0 && !m->smooth_scratch) {
+        sn_status r = pool_alloc((void **)&m->smooth_scratch, sizeof(float) * 3 * (size_t)m->np, m->pool, m->stream,
+                                 "smoothing buffer");
+        if (r != SN_OK) return r;
+    }
+    cudaError_t e = sn::launch_smooth(m->a, m->np, iterations, relaxation, 0.5f * constraint_distance,
+                                      m->smooth_scratch, m->spacing, m->origin, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "smoothing launch");
+    return SN_OK;
+}
+
+sn_status sn_mesh_counts(const sn_mesh *m, int64_t *n_points, int64_t *n_quads, int64_t *n_stencil)
+{
+    if (!m) return fail(SN_EINVAL, "mesh is NULL");
+    if (n_points) *n_points = m->np;
+    if (n_quads) *n_quads = m->nq;
+    if (n_stencil) *n_stencil = m->ns;
+    return SN_OK;
+}
+
+sn_status sn_mesh_device_arrays(const sn_mesh *m, const float **points, const int32_t **quads,
+                                const void **quad_labels, const int64_t **stencil_offsets,
+                                const int32_t **stencil_ids, const float **offsets)
+{
+    if (!m) return fail(SN_EINVAL, "mesh is NULL");
+    if (points) *points = m->a.points;
+    if (quads) *quads = m->a.quads;
+    if (quad_labels) *quad_labels = m->a.quad_labels;
+    if (stencil_offsets) *stencil_offsets = m->a.sten_off;
+    if (stencil_ids) *stencil_ids = m->a.sten_ids;
+    if (offsets) *offsets = m->a.offsets;
+    return SN_OK;
+}
+
+sn_status sn_mesh_face_masks(const sn_mesh *m, const uint8_t **face_masks)
+{
+    if (!m || !face_masks) return fail(SN_EINVAL, "mesh or output is NULL");
+    *face_masks = m->a.face_mask;
+    return SN_OK;
+}
+
+sn_status sn_mesh_copy_to_host(const sn_mesh *m, float *points, int32_t *quads, void *quad_labels,
+                               int64_t *stencil_offsets, int32_t *stencil_ids, float *offsets)
+{
+    if (!m) return fail(SN_EINVAL, "mesh is NULL");
+    struct {
+        void *dst;
+        const void *src;
+        size_t bytes;
+    } cp[] = {
+        {points, m->a.points, sizeof(float) * 3 * (size_t)m->np},
+        {quads, m->a.quads, sizeof(int32_t) * 4 * (size_t)m->nq},
+        {quad_labels, m->a.quad_labels, (size_t)m->type * 2 * (size_t)m->nq},
+        {stencil_offsets, m->a.sten_off, sizeof(int64_t) * (size_t)(m->np + 1)},
+        {stencil_ids, m->a.sten_ids, sizeof(int32_t) * (size_t)m->ns},
+        {offsets, m->a.offsets, sizeof(float) * 3 * (size_t)m->np},
+    };
+    for (auto &c : cp) {
+        if (!c.dst || c.bytes == 0) continue;
+        cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, m->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copy to host");
+    }
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy to host");
+    return SN_OK;
+}
+
+void sn_free(sn_mesh *m)
+{
+    if (!m) return;
+    void *ps[] = {m->a.points, m->a.offsets, m->a.cells, m->a.quads, m->a.quad_labels,
+                  m->a.sten_off, m->a.sten_ids, m->a.face_mask, m->smooth_scratch};
+    for (void *p : ps) pool_free(p, m->stream);
+    std::free(m);
+}
+
+} // extern "C"

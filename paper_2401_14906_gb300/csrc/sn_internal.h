@@ -1,0 +1,105 @@
+// sn_internal.h -- shared declarations of the CUDA path (not part of the ABI).
+//
+// Data layout in device memory (x fastest everywhere):
+//   sample row rs = j + ny*k            (ny*nz rows of the label map)
+//   cell row   rc = (cy+1) + (ny+1)*(cz+1), cy in [-1,ny-1], cz in [-1,nz-1]
+//   every row is W = ceil((nx+1)/32) 32-bit words; bit p of a cell row is the
+//   cell cx = p-1, bit i of a sample row is the sample i.
+//   X/Y/Z planes: bit i of row rs is set iff the x/y/z edge from sample (i,j,k)
+//   is intersected (Sec. 2.2 edge test; Sec. 2.3 Passes 1-2 "triads" as bit
+//   planes).  P plane: bit p of row rc is set iff cell (p-1,cy,cz) has a point.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sn.h"
+
+namespace sn {
+
+enum ClassMode { CLASS_ALL = 0, CLASS_BITMAP = 1, CLASS_SORTED = 2 };
+
+// Label classification of Sec. 2.1 / 3.1: kappa(s) = s if s is selected, else
+// the background value.  CLASS_ALL: every value is its own class (the
+// background value maps to itself).  CLASS_BITMAP: membership bit per value
+// below nbits.  CLASS_SORTED: binary search in a sorted list of selected values.
+struct Classifier {
+    int mode;
+    uint32_t background;
+    const uint32_t *bitmap;
+    uint32_t nbits;
+    const uint32_t *sorted;
+    int64_t nsorted;
+};
+
+struct Geometry {
+    int64_t nx, ny, nz;
+    int64_t W;  // words per row
+    int64_t Rs; // sample rows ny*nz
+    int64_t Rc; // cell rows (ny+1)*(nz+1)
+};
+
+// Device temporaries of one extraction.
+struct ExtractScratch {
+    uint32_t *X, *Y, *Z;  // [Rs][W]
+    uint32_t *P;          // [Rc][W]
+    int32_t *preP;        // [Rc][W] exclusive popcount of P before each word, within the row
+    int32_t *cntP;        // [Rc] points per cell row
+    int32_t *cntS;        // [Rc] stencil entries per cell row
+    int32_t *cntQ;        // [Rc] quads per sample row rs (entries rs >= Rs are 0)
+    int64_t *offP, *offS, *offQ; // [Rc+1] exclusive prefix sums; [Rc] = totals
+    int32_t *scan_flags;  // [tiles] look-back status
+    int64_t *scan_vals;   // [2][3][tiles] aggregate / inclusive values
+    uint32_t *scan_ticket;// 1 counter
+};
+
+// Totals read back by the host after the scan.
+struct DevTotals {
+    int64_t n_points, n_stencil, n_quads;
+    int32_t error; // bit 0: look-back spin limit hit
+    int32_t pad;
+};
+
+// Output arrays of a mesh.
+struct MeshArrays {
+    float *points;       // [np][3] world coordinates
+    float *offsets;      // [np][3] cell-local displacement, voxel units
+    uint64_t *cells;     // [np] packed (cx+1) | (cy+1)<<21 | (cz+1)<<42
+    int32_t *quads;      // [nq][4]
+    void *quad_labels;   // [nq][2] label type
+    int64_t *sten_off;   // [np+1]
+    int32_t *sten_ids;   // [ns]
+    uint8_t *face_mask;  // [np]
+};
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kSpinLimit = 1 << 22;
+
+// launchers (sn_extract.cu)
+cudaError_t launch_planes(int type, const void *labels, const Classifier &c, const Geometry &g,
+                          const ExtractScratch &s, cudaStream_t st);
+cudaError_t launch_cellrows(const Geometry &g, const ExtractScratch &s, cudaStream_t st);
+cudaError_t launch_scan(const Geometry &g, const ExtractScratch &s, DevTotals *totals, cudaStream_t st);
+cudaError_t launch_emit(int type, const void *labels, const Classifier &c, const Geometry &g,
+                        const ExtractScratch &s, const MeshArrays &m, const double spacing[3],
+                        const double origin[3], const DevTotals *tot, cudaStream_t st);
+
+// launchers (sn_smooth.cu)
+cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float relaxation, float half,
+                          float *scratch, const double spacing[3], const double origin[3], cudaStream_t st);
+cudaError_t launch_centres(const MeshArrays &m, int64_t np, const double spacing[3], const double origin[3],
+                           cudaStream_t st);
+
+// profiling (sn_api.cu)
+struct ProfScope {
+    ProfScope(const char *name, cudaStream_t st);
+    ~ProfScope();
+    const char *name_;
+    cudaStream_t st_;
+    cudaEvent_t a_, b_;
+    bool on_;
+};
+
+} // namespace sn

@@ -1,0 +1,244 @@
+"""Thin ctypes binding of libsn.so with the same names as the C ABI (include/sn.h).
+
+Argument marshalling only: every step of extraction and smoothing runs in the
+library's CUDA kernels.  PyTorch is used for device memory and streams.  If
+libsn.so is missing or cannot be loaded, every call raises; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libsn.so")
+
+SN_OK, SN_EINVAL, SN_ENOMEM, SN_EOVERFLOW, SN_ECUDA, SN_ETIMEOUT = range(6)
+SN_U8, SN_U16, SN_U32 = 1, 2, 4
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SNError(RuntimeError):
+    def __init__(self, status, detail):
+        self.status = status
+        super().__init__(f"{status_string(status)} ({detail})" if detail else status_string(status))
+
+
+class sn_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+# every symbol declared in include/sn.h, with its ctypes signature
+_P = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_DP = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "sn_extract": (ctypes.c_int, [_P, ctypes.c_int, _I64P, _DP, _DP, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int64,
+                                  ctypes.c_uint32, _P, ctypes.POINTER(_P)]),
+    "sn_smooth": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_float, ctypes.c_float]),
+    "sn_mesh_counts": (ctypes.c_int, [_P, _I64P, _I64P, _I64P]),
+    "sn_mesh_device_arrays": (ctypes.c_int, [_P] + [ctypes.POINTER(_P)] * 6),
+    "sn_mesh_face_masks": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "sn_mesh_copy_to_host": (ctypes.c_int, [_P] + [_P] * 6),
+    "sn_free": (None, [_P]),
+    "sn_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "sn_last_error": (ctypes.c_char_p, []),
+    "sn_profile_enable": (None, [ctypes.c_int]),
+    "sn_profile_read": (ctypes.c_int, [ctypes.POINTER(sn_kernel_time), ctypes.c_int, ctypes.c_int]),
+}
+
+
+def load(path: str | None = None):
+    """Load libsn.so (build it first with paper_2401_14906_gb300.build.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"libsn.so not found at {p}: build it with "
+                                   "`python -m paper_2401_14906_gb300.build` (nvcc, sm_103a)")
+            lib = ctypes.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def status_string(s):
+    return load().sn_status_string(int(s)).decode()
+
+
+def sn_last_error():
+    return load().sn_last_error().decode()
+
+
+def _check(rc):
+    if rc != SN_OK:
+        raise SNError(rc, sn_last_error())
+
+
+_NP_TYPE = {np.dtype(np.uint8): SN_U8, np.dtype(np.uint16): SN_U16, np.dtype(np.uint32): SN_U32}
+_NP_OF = {SN_U8: np.uint8, SN_U16: np.uint16, SN_U32: np.uint32}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _label_info(labels):
+    """(pointer, type code, dims (nx,ny,nz), is_cuda, keepalive) for a (nz,ny,nx) array/tensor."""
+    if isinstance(labels, np.ndarray):
+        a = np.ascontiguousarray(labels)
+        if a.dtype not in _NP_TYPE or a.ndim != 3:
+            raise ValueError("labels must be a 3-D uint8/uint16/uint32 array shaped (nz, ny, nx)")
+        nz, ny, nx = a.shape
+        return a.ctypes.data, _NP_TYPE[a.dtype], (nx, ny, nz), False, a
+    torch = _torch()
+    t = labels
+    tmap = {torch.uint8: SN_U8, torch.uint16: SN_U16, torch.uint32: SN_U32}
+    if t.dtype not in tmap or t.dim() != 3:
+        raise ValueError("labels must be a 3-D uint8/uint16/uint32 tensor shaped (nz, ny, nx)")
+    if not t.is_contiguous():
+        t = t.contiguous()
+    nz, ny, nx = t.shape
+    return t.data_ptr(), tmap[t.dtype], (nx, ny, nz), t.is_cuda, t
+
+
+def _stream_handle(stream, is_cuda):
+    if stream is None:
+        if is_cuda:
+            return _torch().cuda.current_stream().cuda_stream
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Mesh:
+    """Owner of an sn_mesh*; freed by free() or when garbage-collected."""
+
+    def __init__(self, handle, label_type, dims, spacing, origin):
+        self._h = ctypes.c_void_p(handle)
+        self.label_type = label_type
+        self.dims = dims
+        self.spacing = tuple(spacing)
+        self.origin = tuple(origin)
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("mesh has been freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            load().sn_free(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def counts(self):
+        return sn_mesh_counts(self)
+
+
+def sn_extract(labels, spacing=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0), selected=None, background=0,
+               stream=None) -> Mesh:
+    """Extract the shared quad mesh of a (nz, ny, nx) label map (device tensor or host array)."""
+    lib = load()
+    ptr, tcode, dims, is_cuda, keep = _label_info(labels)
+    d = (ctypes.c_int64 * 3)(*dims)
+    sp = (ctypes.c_double * 3)(*[float(s) for s in spacing])
+    org = (ctypes.c_double * 3)(*[float(o) for o in origin])
+    sel_ptr, nsel, sel_keep = None, 0, None
+    if selected is not None:
+        sel_keep = np.ascontiguousarray(np.asarray(selected, dtype=np.uint32))
+        sel_ptr = sel_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+        nsel = int(sel_keep.size)
+    out = ctypes.c_void_p()
+    rc = lib.sn_extract(ctypes.c_void_p(ptr), tcode, d, sp, org, sel_ptr, nsel, int(background),
+                        ctypes.c_void_p(_stream_handle(stream, is_cuda)), ctypes.byref(out))
+    del keep, sel_keep
+    _check(rc)
+    return Mesh(out.value, tcode, dims, spacing, origin)
+
+
+def sn_smooth(mesh: Mesh, iterations=16, relaxation=0.5, constraint_distance=1.0):
+    _check(load().sn_smooth(mesh.handle, int(iterations), float(relaxation), float(constraint_distance)))
+
+
+def sn_mesh_counts(mesh: Mesh):
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().sn_mesh_counts(mesh.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def sn_mesh_copy_to_host(mesh: Mesh):
+    """All output arrays as numpy arrays (waits for the mesh's stream)."""
+    n, q, s = sn_mesh_counts(mesh)
+    out = {
+        "points": np.empty((n, 3), np.float32),
+        "quads": np.empty((q, 4), np.int32),
+        "quad_labels": np.empty((q, 2), _NP_OF[mesh.label_type]),
+        "stencil_offsets": np.empty(n + 1, np.int64),
+        "stencil_ids": np.empty(s, np.int32),
+        "offsets": np.empty((n, 3), np.float32),
+    }
+    order = ["points", "quads", "quad_labels", "stencil_offsets", "stencil_ids", "offsets"]
+    _check(load().sn_mesh_copy_to_host(mesh.handle, *[ctypes.c_void_p(out[k].ctypes.data) for k in order]))
+    return out
+
+
+class _CudaArray:
+    """Zero-copy view of a borrowed device pointer for torch.as_tensor."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def sn_mesh_device_arrays(mesh: Mesh):
+    """Borrowed device arrays as torch tensors (valid until the mesh is freed)."""
+    torch = _torch()
+    n, q, s = sn_mesh_counts(mesh)
+    ptrs = [ctypes.c_void_p() for _ in range(6)]
+    _check(load().sn_mesh_device_arrays(mesh.handle, *[ctypes.byref(p) for p in ptrs]))
+    lt = {SN_U8: "|u1", SN_U16: "<u2", SN_U32: "<u4"}[mesh.label_type]
+    spec = [("points", (n, 3), "<f4"), ("quads", (q, 4), "<i4"), ("quad_labels", (q, 2), lt),
+            ("stencil_offsets", (n + 1,), "<i8"), ("stencil_ids", (s,), "<i4"), ("offsets", (n, 3), "<f4")]
+    out = {}
+    for (name, shape, ts), p in zip(spec, ptrs):
+        out[name] = torch.as_tensor(_CudaArray(p.value, shape, ts), device="cuda")
+    fm = ctypes.c_void_p()
+    _check(load().sn_mesh_face_masks(mesh.handle, ctypes.byref(fm)))
+    out["face_masks"] = torch.as_tensor(_CudaArray(fm.value, (n,), "|u1"), device="cuda")
+    return out
+
+
+def sn_mesh_face_masks_host(mesh: Mesh):
+    t = sn_mesh_device_arrays(mesh)["face_masks"]
+    return t.cpu().numpy()
+
+
+def sn_profile_enable(on=True):
+    load().sn_profile_enable(1 if on else 0)
+
+
+def sn_profile_read(reset=False):
+    """{kernel name: (launches, total_ms)} accumulated since the last reset."""
+    lib = load()
+    buf = (sn_kernel_time * 64)()
+    n = lib.sn_profile_read(buf, 64, 1 if reset else 0)
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n, 64))}

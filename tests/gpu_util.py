@@ -1,0 +1,74 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI and
+compare it with the oracle element by element."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+# Tolerances.  Integer arrays and the unsmoothed points (a single FP32 rounding
+# of the FP64 cell centre) must be bit-exact.  Smoothed offsets are FP32 and
+# must be within 1e-5 voxel of the FP64 oracle (the stated target).  Smoothed
+# world points are compared per axis within 1e-5 * spacing plus one FP32 ulp of
+# the coordinate (the final rounding to float).
+OFFSET_TOL = 1e-5
+
+
+def run_gpu(labels, spacing=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0), selected=None, background=0, iterations=16,
+            relaxation=0.5, constraint=1.0, on_device=True):
+    import torch
+
+    from paper_2401_14906_gb300 import sn
+    if on_device:
+        t = torch.from_numpy(np.ascontiguousarray(labels).view(
+            {1: np.uint8, 2: np.int16, 4: np.int32}[labels.dtype.itemsize])).cuda()
+        t = t.view({1: torch.uint8, 2: torch.uint16, 4: torch.uint32}[labels.dtype.itemsize])
+        src = t
+    else:
+        src = np.ascontiguousarray(labels)
+    m = sn.sn_extract(src, spacing, origin, selected=selected, background=background)
+    ext = sn.sn_mesh_copy_to_host(m)
+    ext["face_masks"] = sn.sn_mesh_face_masks_host(m)
+    smo = None
+    if iterations is not None:
+        sn.sn_smooth(m, iterations, relaxation, constraint)
+        smo = sn.sn_mesh_copy_to_host(m)
+    m.free()
+    return ext, smo
+
+
+def compare_extract(gpu, ref):
+    assert gpu["points"].shape[0] == ref.n_points
+    assert gpu["quads"].shape[0] == ref.n_quads
+    assert gpu["stencil_ids"].shape[0] == ref.n_stencil
+    np.testing.assert_array_equal(gpu["points"], ref.points.astype(np.float32))
+    np.testing.assert_array_equal(gpu["quads"], ref.quads)
+    np.testing.assert_array_equal(gpu["quad_labels"], ref.quad_labels)
+    np.testing.assert_array_equal(gpu["stencil_offsets"], ref.stencil_offsets)
+    np.testing.assert_array_equal(gpu["stencil_ids"], ref.stencil_ids)
+    np.testing.assert_array_equal(gpu["face_masks"], ref.face_masks)
+    assert np.all(gpu["offsets"] == 0.0)
+
+
+def compare_smooth(gpu, ref_off, ref_pts, spacing, constraint):
+    off = gpu["offsets"].astype(np.float64)
+    err = np.abs(off - ref_off)
+    assert err.size == 0 or err.max() <= OFFSET_TOL, f"max offset error {err.max():.3e} voxel"
+    h = 0.5 * constraint
+    assert np.all(np.abs(gpu["offsets"]) <= np.float32(h))
+    pts = gpu["points"].astype(np.float64)
+    tol = OFFSET_TOL * np.asarray(spacing)[None, :] + np.spacing(np.abs(ref_pts).astype(np.float32)).astype(
+        np.float64)
+    assert np.all(np.abs(pts - ref_pts) <= tol)
+
+
+def parity(labels, spacing=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0), selected=None, background=0, iterations=16,
+           relaxation=0.5, constraint=1.0, on_device=True):
+    gpu_e, gpu_s = run_gpu(labels, spacing, origin, selected, background, iterations, relaxation, constraint,
+                           on_device)
+    ref = oracle.extract(labels, spacing, origin, selected, background)
+    compare_extract(gpu_e, ref)
+    if iterations is not None:
+        ref_off, ref_pts = oracle.smooth(ref, spacing, origin, iterations, relaxation, constraint)
+        compare_smooth(gpu_s, ref_off, ref_pts, spacing, constraint)
+    return ref

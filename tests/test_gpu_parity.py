@@ -1,0 +1,115 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Integer outputs and unsmoothed points are bit-exact; smoothed offsets are
+within 1e-5 voxel.  Sizes span several 32-bit words per row, ragged row tails,
+every label width, selected-label modes and the degenerate cases.
+"""
+import numpy as np
+import pytest
+
+import sn_synth
+from gpu_util import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_14906_gb300 import build
+    build.build()
+
+
+def test_config1_full():
+    w = sn_synth.config1()
+    ref = parity(w.labels, w.spacing, w.origin, iterations=w.iterations, relaxation=w.relaxation,
+                 constraint=w.constraint)
+    assert ref.n_points > 5000
+
+
+@pytest.mark.parametrize("nx", [1, 2, 31, 32, 33, 63, 64, 65, 100, 127, 129, 1023, 1024, 1025])
+def test_ragged_rows(nx):
+    rng = np.random.default_rng(nx)
+    lab = (rng.random((5, 4, nx)) < 0.3).astype(np.uint16) * rng.integers(1, 5, size=(5, 4, nx)).astype(np.uint16)
+    parity(lab, iterations=5)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16, np.uint32])
+@pytest.mark.parametrize("seed", range(4))
+def test_random_maps(dtype, seed):
+    rng = np.random.default_rng(1000 + seed)
+    shape = tuple(int(s) for s in rng.integers(1, 40, size=3))
+    lab = rng.integers(0, 4, size=shape).astype(dtype)
+    parity(lab, spacing=(0.7, 1.3, 2.0), origin=(-5.0, 3.0, 100.0), iterations=7, relaxation=0.6, constraint=0.8)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16, np.uint32])
+def test_ellipsoids_each_dtype(dtype):
+    lab = sn_synth.ellipsoids((70, 45, 38), 6, 4.0, 15.0, dtype, seed=9)
+    parity(lab, iterations=16)
+
+
+def test_selected_bitmap_mode():
+    lab = sn_synth.ellipsoids((60, 50, 40), 8, 4.0, 14.0, np.uint16, seed=4)
+    parity(lab, selected=[2, 5, 7], background=0, iterations=9)
+    parity(lab, selected=[1, 2, 3, 4, 5, 6, 7, 8], background=0, iterations=3)
+
+
+def test_selected_sorted_mode_large_u32_labels():
+    base = sn_synth.ellipsoids((48, 40, 36), 6, 4.0, 14.0, np.uint32, seed=5)
+    lab = np.where(base > 0, base.astype(np.uint64) * 700_000_000 % (2**32 - 3) + 2, 0).astype(np.uint32)
+    vals = sorted(set(np.unique(lab).tolist()) - {0})
+    parity(lab, selected=vals[::2], background=0, iterations=4)
+    parity(lab, selected=vals[1:4], background=7, iterations=4)
+
+
+def test_background_value_nonzero_and_max_labels():
+    for dtype in (np.uint8, np.uint16, np.uint32):
+        top = np.iinfo(dtype).max
+        lab = np.full((9, 8, 37), top, dtype=dtype)
+        lab[2:6, 1:7, 3:30] = top - 1
+        lab[4, 4, 10:20] = 0
+        parity(lab, background=int(top), iterations=4)
+        parity(lab, selected=[int(top) - 1], background=int(top), iterations=4)
+
+
+def test_degenerate_and_empty():
+    for shape in [(1, 1, 1), (1, 1, 40), (1, 33, 1), (2, 1, 1), (1, 2, 2), (3, 1, 70)]:
+        lab = (np.arange(int(np.prod(shape))).reshape(shape) % 3).astype(np.uint8)
+        parity(lab, iterations=3)
+    ref = parity(np.zeros((6, 7, 8), np.uint16), iterations=5)
+    assert ref.n_points == 0
+    z, y, x = np.mgrid[0:7, 0:6, 0:45]
+    parity(((x + y + z) % 2).astype(np.uint8), iterations=5)
+
+
+def test_host_labels_are_copied():
+    lab = sn_synth.ellipsoids((50, 40, 30), 5, 4.0, 12.0, np.uint16, seed=6)
+    parity(lab, iterations=8, on_device=False)
+
+
+def test_zero_iterations_and_zero_relaxation():
+    lab = sn_synth.ellipsoids((40, 40, 40), 4, 4.0, 12.0, np.uint16, seed=8)
+    parity(lab, iterations=0)
+    parity(lab, iterations=5, relaxation=0.0)
+    parity(lab, iterations=6, relaxation=1.0, constraint=0.0)
+
+
+def test_determinism():
+    from gpu_util import run_gpu
+    lab = sn_synth.ellipsoids((64, 64, 64), 6, 6.0, 20.0, np.uint16, seed=10)
+    a = run_gpu(lab)
+    b = run_gpu(lab)
+    for k in a[0]:
+        np.testing.assert_array_equal(a[0][k], b[0][k])
+    for k in a[1]:
+        np.testing.assert_array_equal(a[1][k], b[1][k])
+
+
+def test_config2_full_size():
+    w = sn_synth.config2()
+    ref = parity(w.labels, w.spacing, w.origin, iterations=w.iterations, relaxation=w.relaxation,
+                 constraint=w.constraint)
+    assert ref.n_points > 1_000_000
