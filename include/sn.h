@@ -99,6 +99,39 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
  */
 sn_status sn_smooth(sn_mesh *m, int iterations, float relaxation, float constraint_distance);
 
+/*
+ * sn_smooth_static -- the sweeps of sn_smooth on caller-owned arrays, with no
+ * device allocation.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- programs that reserve all device memory
+ * up front through their own allocator and forbid other allocations, real-time
+ * pipelines that must not allocate after start-up (an allocation can
+ * synchronise the device and stall them), and plugins inside an application
+ * that owns the GPU's memory.
+ *
+ * stencil_offsets int64 [n_points+1], stencil_ids int32, face_masks uint8
+ *             [n_points]: device arrays laid out as sn_mesh_device_arrays and
+ *             sn_mesh_face_masks return them (read-only, caller-owned).
+ * offsets     device float [n_points][3], caller-owned: receives the smoothed
+ *             displacement of each point from its cell centre, in voxels.
+ * iterations, relaxation, constraint_distance: as for sn_smooth.
+ * cuda_stream the stream the sweeps are enqueued on; returns without waiting.
+ *
+ * The second buffer of the double buffer is a fixed array inside the library
+ * of SN_STATIC_MAX_POINTS points (12 MiB), kept by every GPU that loads the
+ * library until the process exits.  n_points above SN_STATIC_MAX_POINTS is
+ * rejected with SN_EINVAL.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture.  Every call shares the array and it
+ * keeps the last call's contents (each call clears what it reads first).
+ * Calls whose GPU work overlaps -- on different streams or from different host
+ * threads -- race on the array: issue them in order on one stream.  Errors:
+ * SN_EINVAL, SN_ECUDA; sn_last_error() has the detail.
+ */
+#define SN_STATIC_MAX_POINTS 1048576
+sn_status sn_smooth_static(const int64_t *stencil_offsets, const int32_t *stencil_ids, const uint8_t *face_masks,
+                           int64_t n_points, int iterations, float relaxation, float constraint_distance,
+                           float *offsets, void *cuda_stream);
+
 /* Output sizes: points, quads, stencil entries (sum of stencil lengths). */
 sn_status sn_mesh_counts(const sn_mesh *m, int64_t *n_points, int64_t *n_quads, int64_t *n_stencil);
 

@@ -120,6 +120,8 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
 namespace sn {
 
+void set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
 ProfScope::ProfScope(const char *name, cudaStream_t st) : name_(name), st_(st), a_(nullptr), b_(nullptr), on_(false)
 {
     if (!g_prof_on.load()) return;

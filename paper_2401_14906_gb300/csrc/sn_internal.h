@@ -92,6 +92,9 @@ cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float
 cudaError_t launch_centres(const MeshArrays &m, int64_t np, const double spacing[3], const double origin[3],
                            cudaStream_t st);
 
+// detail message returned by sn_last_error() on this thread (sn_api.cu)
+void set_last_error(const char *msg);
+
 // profiling (sn_api.cu)
 struct ProfScope {
     ProfScope(const char *name, cudaStream_t st);

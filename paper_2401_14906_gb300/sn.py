@@ -48,6 +48,8 @@ SIGNATURES = {
     "sn_free": (None, [_P]),
     "sn_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sn_last_error": (ctypes.c_char_p, []),
+    "sn_smooth_static": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                        _P, _P]),
     "sn_profile_enable": (None, [ctypes.c_int]),
     "sn_profile_read": (ctypes.c_int, [ctypes.POINTER(sn_kernel_time), ctypes.c_int, ctypes.c_int]),
 }
@@ -230,6 +232,18 @@ def sn_mesh_device_arrays(mesh: Mesh):
 def sn_mesh_face_masks_host(mesh: Mesh):
     t = sn_mesh_device_arrays(mesh)["face_masks"]
     return t.cpu().numpy()
+
+
+SN_STATIC_MAX_POINTS = 1048576
+
+
+def sn_smooth_static(stencil_offsets, stencil_ids, face_masks, n_points, iterations, relaxation,
+                     constraint_distance, offsets, stream=None):
+    """Smoothing sweeps on caller-owned device tensors, allocating nothing (see include/sn.h)."""
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    _check(load().sn_smooth_static(ptr(stencil_offsets), ptr(stencil_ids), ptr(face_masks), int(n_points),
+                                   int(iterations), float(relaxation), float(constraint_distance), ptr(offsets),
+                                   ctypes.c_void_p(_stream_handle(stream, True))))
 
 
 def sn_profile_enable(on=True):
