@@ -155,7 +155,8 @@ sn_status sn_mesh_device_arrays(const sn_mesh *m, const float **points, const in
 sn_status sn_mesh_face_masks(const sn_mesh *m, const uint8_t **face_masks);
 
 /* Copies the arrays above into caller-allocated host buffers (any may be NULL)
- * with the layouts of sn_mesh_device_arrays; waits for the mesh's stream. */
+ * with the layouts of sn_mesh_device_arrays; waits for the mesh's stream.
+ * Returns SN_ETIMEOUT if a smoothing launch gave up a bounded wait. */
 sn_status sn_mesh_copy_to_host(const sn_mesh *m, float *points, int32_t *quads, void *quad_labels,
                                int64_t *stencil_offsets, int32_t *stencil_ids, float *offsets);
 

@@ -34,8 +34,8 @@ def sources():
 
 
 def _inputs():
-    return sources() + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(ROOT, "include", "sn.h"),
-                                                               os.path.abspath(__file__)]
+    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+    return sources() + headers + [os.path.join(ROOT, "include", "sn.h"), os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:

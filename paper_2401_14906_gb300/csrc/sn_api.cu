@@ -309,6 +309,7 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
     g.ny = ny;
     g.nz = nz;
     g.W = (nx + 1 + 31) / 32;
+    g.WS = (g.W + 3) / 4 * 4;
     g.Rs = ny * nz;
     g.Rc = (ny + 1) * (nz + 1);
     const int ntiles = (int)((g.Rc + sn::kScanTile - 1) / sn::kScanTile);
@@ -320,11 +321,10 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
         size_t bytes;
         const char *what;
     } plan[] = {
-        {(void **)&s.X, sizeof(uint32_t) * (size_t)(g.Rs * g.W), "X plane"},
-        {(void **)&s.Y, sizeof(uint32_t) * (size_t)(g.Rs * g.W), "Y plane"},
-        {(void **)&s.Z, sizeof(uint32_t) * (size_t)(g.Rs * g.W), "Z plane"},
-        {(void **)&s.P, sizeof(uint32_t) * (size_t)(g.Rc * g.W), "point plane"},
-        {(void **)&s.preP, sizeof(int32_t) * (size_t)(g.Rc * g.W), "point rank plane"},
+        {(void **)&s.X, sizeof(uint32_t) * (size_t)(g.Rs * g.WS), "X plane"},
+        {(void **)&s.Y, sizeof(uint32_t) * (size_t)(g.Rs * g.WS), "Y plane"},
+        {(void **)&s.Z, sizeof(uint32_t) * (size_t)(g.Rs * g.WS), "Z plane"},
+        {(void **)&s.P, sizeof(uint32_t) * (size_t)(g.Rc * g.WS), "point plane"},
         {(void **)&s.cntP, sizeof(int32_t) * (size_t)g.Rc, "point counts"},
         {(void **)&s.cntS, sizeof(int32_t) * (size_t)g.Rc, "stencil counts"},
         {(void **)&s.cntQ, sizeof(int32_t) * (size_t)g.Rc, "quad counts"},
@@ -345,15 +345,24 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
         if (r != SN_OK) return cleanup(), r;
     }
 
-    // Passes 1-3
-    if ((e = sn::launch_planes(type, dlabels, cls, g, s, st)) != cudaSuccess)
-        return cleanup(), cuda_fail(e, "k_planes launch");
-    if ((e = sn::launch_cellrows(g, s, st)) != cudaSuccess) return cleanup(), cuda_fail(e, "k_cellrows launch");
+    // Passes 1-3: one streaming kernel when a tile of rows fits shared memory
+    if ((e = cudaMemsetAsync(dtot, 0, sizeof(sn::DevTotals), st)) != cudaSuccess)
+        return cleanup(), cuda_fail(e, "totals");
+    e = sn::launch_count(type, dlabels, cls, g, s, dtot, st);
+    if (e == cudaErrorNotSupported) {
+        cudaGetLastError();
+        if ((e = sn::launch_planes(type, dlabels, cls, g, s, st)) != cudaSuccess)
+            return cleanup(), cuda_fail(e, "k_planes launch");
+        e = sn::launch_cellrows(g, s, st);
+    }
+    if (e != cudaSuccess) return cleanup(), cuda_fail(e, "counting launch");
     if ((e = sn::launch_scan(g, s, dtot, st)) != cudaSuccess) return cleanup(), cuda_fail(e, "k_scan launch");
     e = cudaMemcpyAsync(htot, dtot, sizeof(sn::DevTotals), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cleanup(), cuda_fail(e, "count read-back");
-    if (htot->error) return cleanup(), fail(SN_ETIMEOUT, "row scan look-back wait limit reached");
+    if (htot->error)
+        return cleanup(), fail(SN_ETIMEOUT, (htot->error & 1) ? "row scan look-back wait limit reached"
+                                                              : "label copy wait limit reached");
     const int64_t np = htot->n_points, nq = htot->n_quads, ns = htot->n_stencil;
     if (np > (int64_t)INT32_MAX) return cleanup(), fail(SN_EOVERFLOW, "more than INT32_MAX points");
 
@@ -385,6 +394,9 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
         {(void **)&m->a.sten_off, sizeof(int64_t) * (size_t)(np + 1), "stencil offsets"},
         {(void **)&m->a.sten_ids, sizeof(int32_t) * (size_t)ns, "stencil ids"},
         {(void **)&m->a.face_mask, (size_t)np, "face masks"},
+        {(void **)&m->a.meta, sizeof(int32_t) * 4, "mesh meta"},
+        {(void **)&m->a.nbr, sizeof(uint2) * (size_t)np, "smoothing neighbours"},
+        {(void **)&m->a.lut_x, sizeof(float2) * (size_t)(nx + ny + nz + 3), "cell-centre tables"},
     };
     for (auto &pl : oplan) {
         sn_status r = pool_alloc(pl.p, pl.bytes, pool, st, pl.what);
@@ -394,8 +406,24 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
         }
     }
 
+    m->a.lut_y = m->a.lut_x + (nx + 1);
+    m->a.lut_z = m->a.lut_y + (ny + 1);
+    if ((e = sn::launch_centre_lut(m->a, dims, spacing, origin, st)) != cudaSuccess) {
+        sn_free(m);
+        return cleanup(), cuda_fail(e, "cell-centre tables");
+    }
+
     // Pass 4
-    if ((e = sn::launch_emit(type, dlabels, cls, g, s, m->a, spacing, origin, dtot, st)) != cudaSuccess) {
+    if ((e = cudaMemsetAsync(m->a.meta, 0, sizeof(int32_t) * 4, st)) != cudaSuccess) {
+        sn_free(m);
+        return cleanup(), cuda_fail(e, "mesh meta");
+    }
+    e = sn::launch_emit_tile(type, dlabels, cls, g, s, m->a, dtot, st);
+    if (e == cudaErrorNotSupported) {
+        cudaGetLastError();
+        e = sn::launch_emit(type, dlabels, cls, g, s, m->a, dtot, st);
+    }
+    if (e != cudaSuccess) {
         sn_free(m);
         return cleanup(), cuda_fail(e, "k_emit launch");
     }
@@ -424,7 +452,7 @@ sn_status sn_smooth(sn_mesh *m, int iterations, float relaxation, float constrai
         if (r != SN_OK) return r;
     }
     cudaError_t e = sn::launch_smooth(m->a, m->np, iterations, relaxation, 0.5f * constraint_distance,
-                                      m->smooth_scratch, m->spacing, m->origin, m->stream);
+                                      m->smooth_scratch, m->spacing, m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "smoothing launch");
     return SN_OK;
 }
@@ -480,16 +508,19 @@ sn_status sn_mesh_copy_to_host(const sn_mesh *m, float *points, int32_t *quads, 
         cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, m->stream);
         if (e != cudaSuccess) return cuda_fail(e, "copy to host");
     }
-    cudaError_t e = cudaStreamSynchronize(m->stream);
+    int32_t meta[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(meta, m->a.meta, sizeof(meta), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "copy to host");
+    if (meta[1]) return fail(SN_ETIMEOUT, "smoothing dependency wait limit reached");
     return SN_OK;
 }
 
 void sn_free(sn_mesh *m)
 {
     if (!m) return;
-    void *ps[] = {m->a.points, m->a.offsets, m->a.cells, m->a.quads, m->a.quad_labels,
-                  m->a.sten_off, m->a.sten_ids, m->a.face_mask, m->smooth_scratch};
+    void *ps[] = {m->a.points,    m->a.offsets, m->a.cells, m->a.quads, m->a.quad_labels, m->a.sten_off,
+                  m->a.sten_ids,  m->a.face_mask, m->a.meta,  m->a.nbr,   m->a.lut_x,       m->smooth_scratch};
     for (void *p : ps) pool_free(p, m->stream);
     std::free(m);
 }

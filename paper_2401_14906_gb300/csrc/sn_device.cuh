@@ -1,0 +1,126 @@
+// sn_device.cuh -- device helpers shared by the extraction kernels.
+#pragma once
+
+#include "sn_internal.h"
+
+namespace sn {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int MODE>
+__device__ __forceinline__ uint32_t kappa(const Classifier &c, uint32_t s)
+{
+    if (MODE == CLASS_ALL) return s;
+    bool member;
+    if (MODE == CLASS_BITMAP) {
+        member = s < c.nbits && ((__ldg(c.bitmap + (s >> 5)) >> (s & 31u)) & 1u);
+    } else {
+        int64_t lo = 0, hi = c.nsorted;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (__ldg(c.sorted + mid) < s) lo = mid + 1;
+            else hi = mid;
+        }
+        member = lo < c.nsorted && __ldg(c.sorted + lo) == s;
+    }
+    return member ? s : c.background;
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t ldlab(const T *p, int64_t i)
+{
+    return (uint32_t)__ldg(p + i);
+}
+
+__device__ __forceinline__ int warp_sum(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int64_t warp_sum64(int64_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ int64_t warp_incl_scan64(int64_t v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// word w of a plane row (row stride WS words), 0 outside the row range or the word range
+__device__ __forceinline__ uint32_t ldw(const uint32_t *plane, int64_t row, int64_t w, int64_t W, int64_t WS)
+{
+    return (row >= 0 && w >= 0 && w < W) ? plane[row * WS + w] : 0u;
+}
+
+__device__ __forceinline__ int64_t sample_row(const Geometry &g, int64_t y, int64_t z)
+{
+    return (y >= 0 && y < g.ny && z >= 0 && z < g.nz) ? (y + g.ny * z) : -1;
+}
+
+__device__ __forceinline__ uint32_t shl1(uint32_t cur, uint32_t prev) { return (cur << 1) | (prev >> 31); }
+
+// ---- mbarrier and bulk (TMA) copies into shared memory
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// bounded wait for the phase `parity` of an mbarrier; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = smem_u32(bar);
+    for (int spin = 0; spin < kSpinLimit; ++spin) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+} // namespace dev
+} // namespace sn

@@ -16,85 +16,13 @@
 //               paper's 3x3 row iterator (Sec. 3.6) computes incrementally.
 // Rows without points or quads return at once: this is the GPU form of the
 // computational trimming of Sec. 3.4.
-#include "sn_internal.h"
+#include "sn_device.cuh"
 
 namespace sn {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-template <int MODE>
-__device__ __forceinline__ uint32_t kappa(const Classifier &c, uint32_t s)
-{
-    if (MODE == CLASS_ALL) return s;
-    bool member;
-    if (MODE == CLASS_BITMAP) {
-        member = s < c.nbits && ((__ldg(c.bitmap + (s >> 5)) >> (s & 31u)) & 1u);
-    } else {
-        int64_t lo = 0, hi = c.nsorted;
-        while (lo < hi) {
-            int64_t mid = (lo + hi) >> 1;
-            if (__ldg(c.sorted + mid) < s) lo = mid + 1;
-            else hi = mid;
-        }
-        member = lo < c.nsorted && __ldg(c.sorted + lo) == s;
-    }
-    return member ? s : c.background;
-}
-
-template <typename T>
-__device__ __forceinline__ uint32_t ldlab(const T *p, int64_t i)
-{
-    return (uint32_t)__ldg(p + i);
-}
-
-__device__ __forceinline__ int warp_sum(int v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
-__device__ __forceinline__ int64_t warp_sum64(int64_t v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
-__device__ __forceinline__ int warp_incl_scan(int v, int lane)
-{
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(kFull, v, o);
-        if (lane >= o) v += t;
-    }
-    return v;
-}
-
-__device__ __forceinline__ int64_t warp_incl_scan64(int64_t v, int lane)
-{
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int64_t t = __shfl_up_sync(kFull, v, o);
-        if (lane >= o) v += t;
-    }
-    return v;
-}
-
-// word w of a plane row, 0 outside the row range or the word range
-__device__ __forceinline__ uint32_t ldw(const uint32_t *plane, int64_t row, int64_t w, int64_t W)
-{
-    return (row >= 0 && w >= 0 && w < W) ? plane[row * W + w] : 0u;
-}
-
-__device__ __forceinline__ int64_t sample_row(const Geometry &g, int64_t y, int64_t z)
-{
-    return (y >= 0 && y < g.ny && z >= 0 && z < g.nz) ? (y + g.ny * z) : -1;
-}
-
-__device__ __forceinline__ uint32_t shl1(uint32_t cur, uint32_t prev) { return (cur << 1) | (prev >> 31); }
+using namespace dev;
 
 struct Faces {
     uint32_t f[6]; // -x, +x, -y, +y, -z, +z
@@ -110,14 +38,15 @@ struct Faces {
 __device__ __forceinline__ Faces cell_faces(const ExtractScratch &s, const Geometry &g, int64_t ra, int64_t rb,
                                             int64_t rcc, int64_t rd, int64_t w)
 {
-    const int64_t W = g.W;
-    uint32_t Xa = ldw(s.X, ra, w, W), Xb = ldw(s.X, rb, w, W), Xc = ldw(s.X, rcc, w, W), Xd = ldw(s.X, rd, w, W);
-    uint32_t Ya = ldw(s.Y, ra, w, W), Yc = ldw(s.Y, rcc, w, W);
-    uint32_t Za = ldw(s.Z, ra, w, W), Zb = ldw(s.Z, rb, w, W);
-    uint32_t pXa = ldw(s.X, ra, w - 1, W), pXb = ldw(s.X, rb, w - 1, W), pXc = ldw(s.X, rcc, w - 1, W),
-             pXd = ldw(s.X, rd, w - 1, W);
-    uint32_t pYa = ldw(s.Y, ra, w - 1, W), pYc = ldw(s.Y, rcc, w - 1, W);
-    uint32_t pZa = ldw(s.Z, ra, w - 1, W), pZb = ldw(s.Z, rb, w - 1, W);
+    const int64_t W = g.W, WS = g.WS;
+    uint32_t Xa = ldw(s.X, ra, w, W, WS), Xb = ldw(s.X, rb, w, W, WS), Xc = ldw(s.X, rcc, w, W, WS),
+             Xd = ldw(s.X, rd, w, W, WS);
+    uint32_t Ya = ldw(s.Y, ra, w, W, WS), Yc = ldw(s.Y, rcc, w, W, WS);
+    uint32_t Za = ldw(s.Z, ra, w, W, WS), Zb = ldw(s.Z, rb, w, W, WS);
+    uint32_t pXa = ldw(s.X, ra, w - 1, W, WS), pXb = ldw(s.X, rb, w - 1, W, WS), pXc = ldw(s.X, rcc, w - 1, W, WS),
+             pXd = ldw(s.X, rd, w - 1, W, WS);
+    uint32_t pYa = ldw(s.Y, ra, w - 1, W, WS), pYc = ldw(s.Y, rcc, w - 1, W, WS);
+    uint32_t pZa = ldw(s.Z, ra, w - 1, W, WS), pZb = ldw(s.Z, rb, w - 1, W, WS);
     Faces F;
     F.f[0] = shl1(Ya | Yc | Za | Zb, pYa | pYc | pZa | pZb);
     F.f[1] = Ya | Yc | Za | Zb;
@@ -142,7 +71,7 @@ __global__ void __launch_bounds__(256) k_planes(const T *__restrict__ lab, Class
     const bool hasY = j + 1 < g.ny, hasZ = k + 1 < g.nz;
     const T *rowY = row + nx;
     const T *rowZ = row + nx * g.ny;
-    uint32_t *Xo = s.X + rs * g.W, *Yo = s.Y + rs * g.W, *Zo = s.Z + rs * g.W;
+    uint32_t *Xo = s.X + rs * g.WS, *Yo = s.Y + rs * g.WS, *Zo = s.Z + rs * g.WS;
     int cnt = 0;
     for (int64_t w = 0; w < g.W; ++w) {
         const int64_t i = w * 32 + lane;
@@ -188,10 +117,7 @@ __global__ void __launch_bounds__(256) k_cellrows(Geometry g, ExtractScratch s)
         }
         const int pc = __popc(pw);
         const int incl = warp_incl_scan(pc, lane);
-        if (w < g.W) {
-            s.P[rc * g.W + w] = pw;
-            s.preP[rc * g.W + w] = carry + incl - pc;
-        }
+        if (w < g.W) s.P[rc * g.WS + w] = pw;
         carry += __shfl_sync(kFull, incl, 31);
         deg_total += warp_sum(deg);
     }
@@ -199,6 +125,326 @@ __global__ void __launch_bounds__(256) k_cellrows(Geometry g, ExtractScratch s)
         s.cntP[rc] = carry;
         s.cntS[rc] = deg_total;
         if (rc >= g.Rs) s.cntQ[rc] = 0;
+    }
+}
+
+// ------------------------------------------- Passes 1-3, one streaming pass
+// k_count: a CTA owns a tile of TY sample rows (j0..j0+TY-1) and KZ slices
+// (k0..k0+KZ-1).  It streams the slices through shared memory -- each slice's
+// TY+1 rows (one halo row) are one contiguous block of the label map, copied by
+// the TMA engine (cp.async.bulk, three-slot ring, one mbarrier per slot) -- and
+// for every slice builds the X/Y/Z words of its rows with warp ballots (Passes
+// 1-2), writes those of the rows it owns, and combines the planes of slices
+// cz and cz+1 (kept in shared memory) into the face and point planes of cell
+// rows (cy, cz) with their point and stencil counts (Pass 3).  Every label is
+// read from HBM once; halo rows and the halo slice come from L2.
+struct CountTiling {
+    int ty, kz;
+    int W;
+    uint64_t wdiv;    // ceil(2^32 / W): it / W == (it * wdiv) >> 32 while it * W < 2^32
+    int slot_bytes;   // bytes of one label slot, rounded up to 128
+    int aligned;      // rows start on 16-byte boundaries: bulk copies allowed
+};
+
+constexpr int kCountSlots = 3;
+constexpr int kCountMaxTY = 16;
+constexpr int kCountHeader = 256; // mbarriers (24 B) + row counters (3*16+2 ints) fit in 256 bytes
+
+// --- edge words of 32 samples from rows in shared memory, packed-integer form.
+// flags16(x): bit 15 / bit 31 set iff the low / high 16-bit half of x is
+// nonzero; flags8(x): bit 7 of each byte set iff that byte is nonzero (the
+// 0x7fff / 0x7f additions cannot carry across halves or bytes).
+__device__ __forceinline__ uint32_t flags16(uint32_t x) { return ((x & 0x7fff7fffu) + 0x7fff7fffu) | x; }
+__device__ __forceinline__ uint32_t flags8(uint32_t x) { return ((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x; }
+// bit 7 of the four bytes of u, packed into bits 0..3
+__device__ __forceinline__ uint32_t nibble(uint32_t u) { return (((u >> 7) & 0x01010101u) * 0x01020408u) >> 24; }
+
+
+// Difference mask of 32 samples of `a` against 32 samples of `b` (or, with
+// SHIFT, against `a` one sample further on).  Samples are read from shared
+// memory as 16-byte vectors; a is followed by at least 4 more bytes.
+template <typename T, bool SHIFT> struct Differ;
+
+template <bool SHIFT> struct Differ<uint16_t, SHIFT> {
+    __device__ static __forceinline__ uint32_t run(const uint16_t *a, const uint16_t *b)
+    {
+        const uint4 *a4 = reinterpret_cast<const uint4 *>(a), *b4 = reinterpret_cast<const uint4 *>(b);
+        uint32_t x[16], any = 0;
+        uint4 na = a4[0];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 va = na;
+            uint4 vb;
+            if (SHIFT) {
+                const uint32_t nxt = q < 3 ? (na = a4[q + 1]).x : reinterpret_cast<const uint32_t *>(a)[16];
+                vb = make_uint4(__byte_perm(va.x, va.y, 0x5432), __byte_perm(va.y, va.z, 0x5432),
+                                __byte_perm(va.z, va.w, 0x5432), __byte_perm(va.w, nxt, 0x5432));
+            } else {
+                if (q < 3) na = a4[q + 1];
+                vb = b4[q];
+            }
+            x[4 * q + 0] = va.x ^ vb.x;
+            x[4 * q + 1] = va.y ^ vb.y;
+            x[4 * q + 2] = va.z ^ vb.z;
+            x[4 * q + 3] = va.w ^ vb.w;
+            any |= x[4 * q] | x[4 * q + 1] | x[4 * q + 2] | x[4 * q + 3];
+        }
+        if (!any) return 0u;
+        uint32_t m = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            m |= nibble(__byte_perm(flags16(x[2 * q]), flags16(x[2 * q + 1]), 0x7531)) << (4 * q);
+        return m;
+    }
+};
+
+template <bool SHIFT> struct Differ<uint8_t, SHIFT> {
+    __device__ static __forceinline__ uint32_t run(const uint8_t *a, const uint8_t *b)
+    {
+        const uint4 *a4 = reinterpret_cast<const uint4 *>(a), *b4 = reinterpret_cast<const uint4 *>(b);
+        uint32_t x[8], any = 0;
+        const uint4 v0 = a4[0], v1 = a4[1];
+        uint4 w0, w1;
+        if (SHIFT) {
+            const uint32_t nxt = reinterpret_cast<const uint32_t *>(a)[8];
+            w0 = make_uint4(__byte_perm(v0.x, v0.y, 0x4321), __byte_perm(v0.y, v0.z, 0x4321),
+                            __byte_perm(v0.z, v0.w, 0x4321), __byte_perm(v0.w, v1.x, 0x4321));
+            w1 = make_uint4(__byte_perm(v1.x, v1.y, 0x4321), __byte_perm(v1.y, v1.z, 0x4321),
+                            __byte_perm(v1.z, v1.w, 0x4321), __byte_perm(v1.w, nxt, 0x4321));
+        } else {
+            w0 = b4[0];
+            w1 = b4[1];
+        }
+        x[0] = v0.x ^ w0.x; x[1] = v0.y ^ w0.y; x[2] = v0.z ^ w0.z; x[3] = v0.w ^ w0.w;
+        x[4] = v1.x ^ w1.x; x[5] = v1.y ^ w1.y; x[6] = v1.z ^ w1.z; x[7] = v1.w ^ w1.w;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) any |= x[k];
+        if (!any) return 0u;
+        uint32_t m = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) m |= nibble(flags8(x[k])) << (4 * k);
+        return m;
+    }
+};
+
+template <bool SHIFT> struct Differ<uint32_t, SHIFT> {
+    __device__ static __forceinline__ uint32_t run(const uint32_t *a, const uint32_t *b)
+    {
+        const uint4 *a4 = reinterpret_cast<const uint4 *>(a), *b4 = reinterpret_cast<const uint4 *>(b);
+        uint32_t m = 0;
+        uint4 na = a4[0];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint4 va = na;
+            uint4 vb;
+            if (SHIFT) {
+                const uint32_t nxt = q < 7 ? (na = a4[q + 1]).x : a[32];
+                vb = make_uint4(va.y, va.z, va.w, nxt);
+            } else {
+                if (q < 7) na = a4[q + 1];
+                vb = b4[q];
+            }
+            m |= ((uint32_t)(va.x != vb.x) | ((uint32_t)(va.y != vb.y) << 1) | ((uint32_t)(va.z != vb.z) << 2) |
+                  ((uint32_t)(va.w != vb.w) << 3))
+                 << (4 * q);
+        }
+        return m;
+    }
+};
+
+// X/Y/Z words of samples [32w, 32w+32) of a row held in shared memory.
+// Fast form (every value its own class, rows on 16-byte boundaries): packed
+// compares; otherwise one classified sample at a time.
+template <typename T, int MODE, bool FAST>
+__device__ __forceinline__ void edge_words(const Classifier &c, const T *row, const T *rowY, const T *rowZ, int64_t nx,
+                                           int w, bool doY, bool doZ, uint32_t &X, uint32_t &Y, uint32_t &Z)
+{
+    const int i0 = w * 32;
+    const int nv = (int)(nx - i0); // valid samples in this word (may exceed 32)
+    const uint32_t mv = nv >= 32 ? 0xffffffffu : (nv <= 0 ? 0u : ((1u << nv) - 1u));
+    const uint32_t mx = nv - 1 >= 32 ? 0xffffffffu : (nv - 1 <= 0 ? 0u : ((1u << (nv - 1)) - 1u));
+    if (FAST) {
+        X = Differ<T, true>::run(row + i0, nullptr) & mx;
+        Y = doY ? (Differ<T, false>::run(row + i0, rowY + i0) & mv) : 0u;
+        Z = doZ ? (Differ<T, false>::run(row + i0, rowZ + i0) & mv) : 0u;
+    } else {
+        X = Y = Z = 0u;
+        for (int b = 0; b < 32; ++b) {
+            const int64_t i = i0 + b;
+            if (i >= nx) break;
+            const uint32_t a = kappa<MODE>(c, (uint32_t)row[i]);
+            if (i + 1 < nx && a != kappa<MODE>(c, (uint32_t)row[i + 1])) X |= 1u << b;
+            if (doY && a != kappa<MODE>(c, (uint32_t)rowY[i])) Y |= 1u << b;
+            if (doZ && a != kappa<MODE>(c, (uint32_t)rowZ[i])) Z |= 1u << b;
+        }
+    }
+}
+
+template <typename T, int MODE, bool FAST>
+__global__ void __launch_bounds__(256, 4) k_count(const T *__restrict__ lab, Classifier c, Geometry g, ExtractScratch s,
+                                               CountTiling tl, DevTotals *tot)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int TY = tl.ty, W = tl.W, tid = threadIdx.x, nthr = blockDim.x;
+    const int64_t nx = g.nx, ny = g.ny, nz = g.nz;
+    const int64_t j0 = (int64_t)blockIdx.x * TY, k0 = (int64_t)blockIdx.y * tl.kz;
+    const int rows_ld = (int)((j0 + TY + 1 <= ny) ? TY + 1 : ny - j0); // rows of a slice block
+    const int rows_own = rows_ld < TY ? rows_ld : TY;
+    const int64_t k_own_end = (k0 + tl.kz < nz) ? k0 + tl.kz : nz;      // owned slices [k0, k_own_end)
+    const int64_t k_ld_end = (k0 + tl.kz < nz) ? k0 + tl.kz + 1 : nz;   // loaded slices [k0, k_ld_end)
+    const int extra = (j0 == 0) ? 1 : 0;                                 // the first tile also owns cy = -1
+
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    int32_t *cnt = reinterpret_cast<int32_t *>(smem + 32); // [0..TY): quads, [TY..2TY+1): points, [..): stencil
+    uint8_t *slots = smem + kCountHeader;
+    uint32_t *planes = reinterpret_cast<uint32_t *>(slots + (size_t)kCountSlots * tl.slot_bytes);
+    const int plane_words = 3 * (TY + 1) * W;
+    auto PL = [&](int buf, int p, int r) -> uint32_t * {
+        return planes + (size_t)buf * plane_words + (p * (TY + 1) + r) * W;
+    };
+
+    const uint32_t slice_bytes = (uint32_t)(rows_ld * nx * (int64_t)sizeof(T));
+    auto issue = [&](int64_t kk) {
+        if (kk >= k_ld_end) return;
+        const int slot = (int)((kk - k0) % kCountSlots);
+        const T *src = lab + (kk * ny + j0) * nx;
+        T *dst = reinterpret_cast<T *>(slots + (size_t)slot * tl.slot_bytes);
+        if (tl.aligned) {
+            if (tid == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&bars[slot], slice_bytes);
+                bulk_load(dst, src, slice_bytes, &bars[slot]);
+            }
+        } else {
+            const int64_t n = (int64_t)rows_ld * nx;
+            for (int64_t e = tid; e < n; e += nthr) dst[e] = src[e];
+        }
+    };
+
+    if (tid == 0) {
+        for (int q = 0; q < kCountSlots; ++q) mbar_init(&bars[q], 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    for (int e = tid; e < 2 * plane_words; e += nthr) planes[e] = 0u;
+    __syncthreads();
+    for (int q = 0; q < kCountSlots; ++q) issue(k0 + q);
+    if (!tl.aligned) __syncthreads();
+
+    uint32_t phase_bits = 0; // parity of the next completion of each slot
+    bool failed = false;
+    int cur = 0;
+    const int64_t k_step_end = (k0 + tl.kz < nz) ? k0 + tl.kz : nz; // kk == nz: zero planes (cz = nz-1)
+    for (int64_t kk = k0; kk <= k_step_end; ++kk) {
+        const bool have = kk < k_ld_end;
+        const bool have_next = kk + 1 < k_ld_end && kk < k_own_end;
+        if (tl.aligned && tid == 0) { // one thread waits; the barrier below releases the others
+            for (int d = 0; d < 2; ++d) {
+                const int64_t kq = kk + d;
+                if ((d == 0 && !have) || (d == 1 && !have_next)) continue;
+                const int slot = (int)((kq - k0) % kCountSlots);
+                if (!failed && !mbar_wait(&bars[slot], (phase_bits >> slot) & 1u)) {
+                    failed = true;
+                    atomicOr(&tot->error, 2);
+                }
+            }
+        }
+        for (int e = tid; e < 3 * TY + 2; e += nthr) cnt[e] = 0;
+        const T *S0 = reinterpret_cast<const T *>(slots + (size_t)((kk - k0) % kCountSlots) * tl.slot_bytes);
+        const T *S1 = reinterpret_cast<const T *>(slots + (size_t)((kk + 1 - k0) % kCountSlots) * tl.slot_bytes);
+        __syncthreads();
+        // ---- Passes 1-2 for slice kk: one thread per (row, word)
+        for (int it = tid; it < (TY + 1) * W; it += nthr) {
+            const int r = (int)(((uint64_t)(uint32_t)it * tl.wdiv) >> 32), w = it - r * W;
+            uint32_t xw = 0, yw = 0, zw = 0;
+            if (have && r < rows_ld) {
+                const T *row = S0 + (int64_t)r * nx;
+                const bool doY = r < rows_own && r + 1 < rows_ld;
+                edge_words<T, MODE, FAST>(c, row, row + nx, S1 + (int64_t)r * nx, nx, w, doY, have_next, xw, yw, zw);
+                if (r < rows_own && (xw | yw | zw)) atomicAdd(&cnt[r], __popc(xw) + __popc(yw) + __popc(zw));
+            }
+            PL(cur, 0, r)[w] = xw;
+            PL(cur, 1, r)[w] = yw;
+            PL(cur, 2, r)[w] = zw;
+        }
+        __syncthreads();
+        // ---- owned sample rows of slice kk: planes and quad counts to global memory
+        if (kk < k_own_end) {
+            for (int it = tid; it < rows_own * W; it += nthr) {
+                const int r = (int)(((uint64_t)(uint32_t)it * tl.wdiv) >> 32), w = it - r * W;
+                const int64_t rs = (j0 + r) + ny * kk;
+                s.X[rs * g.WS + w] = PL(cur, 0, r)[w];
+                s.Y[rs * g.WS + w] = PL(cur, 1, r)[w];
+                s.Z[rs * g.WS + w] = PL(cur, 2, r)[w];
+            }
+            for (int r = tid; r < rows_own; r += nthr) s.cntQ[(j0 + r) + ny * kk] = cnt[r];
+        }
+        // ---- Pass 3 for cell rows (cy, cz = kk-1): sample rows cy, cy+1 of slices cz (prev) and cz+1 (cur)
+        const int64_t cz = kk - 1;
+        const bool do_cells = cz >= k0 || cz == -1;
+        if (do_cells) {
+            const int prev = cur ^ 1;
+            const int nrows = rows_own + extra;
+            for (int it = tid; it < nrows * W; it += nthr) {
+                const int q = (int)(((uint64_t)(uint32_t)it * tl.wdiv) >> 32), w = it - q * W;
+                const int cr = q - extra; // local sample row of cy (-1 for cy = -1)
+                const bool ra = cr >= 0, rb = cr + 1 < rows_ld;
+                uint32_t v[8], p8[8];
+#pragma unroll
+                for (int d = 0; d < 2; ++d) {
+                    const int ww = w - d;
+                    uint32_t *o = d ? p8 : v;
+                    const bool ok = ww >= 0;
+                    // a = (cy, cz), b = (cy+1, cz), c = (cy, cz+1), d = (cy+1, cz+1)
+                    o[0] = (ok && ra) ? PL(prev, 0, cr)[ww] : 0u;
+                    o[2] = (ok && ra) ? PL(cur, 0, cr)[ww] : 0u;
+                    o[4] = (ok && ra) ? PL(prev, 1, cr)[ww] : 0u;
+                    o[5] = (ok && ra) ? PL(cur, 1, cr)[ww] : 0u;
+                    o[6] = (ok && ra) ? PL(prev, 2, cr)[ww] : 0u;
+                    o[1] = (ok && rb) ? PL(prev, 0, cr + 1)[ww] : 0u;
+                    o[3] = (ok && rb) ? PL(cur, 0, cr + 1)[ww] : 0u;
+                    o[7] = (ok && rb) ? PL(prev, 2, cr + 1)[ww] : 0u;
+                }
+                const uint32_t Xa = v[0], Xb = v[1], Xc = v[2], Xd = v[3], Ya = v[4], Yc = v[5], Za = v[6], Zb = v[7];
+                uint32_t F[6];
+                F[0] = shl1(Ya | Yc | Za | Zb, p8[4] | p8[5] | p8[6] | p8[7]);
+                F[1] = Ya | Yc | Za | Zb;
+                F[2] = shl1(Xa | Xc | Za, p8[0] | p8[2] | p8[6]) | Za;
+                F[3] = shl1(Xb | Xd | Zb, p8[1] | p8[3] | p8[7]) | Zb;
+                F[4] = shl1(Xa | Xb | Ya, p8[0] | p8[1] | p8[4]) | Ya;
+                F[5] = shl1(Xc | Xd | Yc, p8[2] | p8[3] | p8[5]) | Yc;
+                uint32_t pw = 0;
+                int deg = 0;
+#pragma unroll
+                for (int f = 0; f < 6; ++f) {
+                    pw |= F[f];
+                    deg += __popc(F[f]);
+                }
+                const int64_t cy = j0 + cr;
+                const int64_t rc = (cy + 1) + (ny + 1) * (cz + 1);
+                s.P[rc * g.WS + w] = pw;
+                if (pw) {
+                    atomicAdd(&cnt[TY + q], __popc(pw));
+                    atomicAdd(&cnt[2 * TY + 1 + q], deg);
+                }
+            }
+        }
+        __syncthreads();
+        if (do_cells) {
+            for (int q = tid; q < rows_own + extra; q += nthr) {
+                const int64_t cy = j0 + q - extra;
+                const int64_t rc = (cy + 1) + (ny + 1) * (cz + 1);
+                s.cntP[rc] = cnt[TY + q];
+                s.cntS[rc] = cnt[2 * TY + 1 + q];
+            }
+        }
+        // slice kk's slot is free: refill it with slice kk + kCountSlots
+        if (have) {
+            const int slot = (int)((kk - k0) % kCountSlots);
+            phase_bits ^= 1u << slot;
+            issue(kk + kCountSlots);
+        }
+        __syncthreads(); // the counters are read above and cleared at the top of the next step
+        cur ^= 1;        // the next step overwrites every row of this buffer
     }
 }
 
@@ -332,156 +578,237 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Geometry g, ExtractScratc
 }
 
 // -------------------------------------------------------------- Pass 4
-__device__ __forceinline__ int32_t rank_in_row(const ExtractScratch &s, int64_t W, int64_t r, int64_t p)
-{
-    if (r < 0 || p < 0 || (p >> 5) >= W) return -1; // cannot happen for a consistent face case
-    const int64_t w = p >> 5;
-    const uint32_t b = (uint32_t)(p & 31);
-    return (int32_t)(s.offP[r] + s.preP[r * W + w] + __popc(s.P[r * W + w] & ((1u << b) - 1u)));
-}
+constexpr int kEmitWarps = 8;
+constexpr int kSeg = 32; // words per row segment (1024 cells)
 
-__device__ __forceinline__ float centre_coord(double origin, double spacing, int64_t c)
-{
-    return __double2float_rn(__dadd_rn(origin, __dmul_rn(spacing, (double)c + 0.5)));
-}
+// Per-warp staging of one 1024-cell segment.  Rows: 0 = (cy,cz), 1 = (cy-1,cz),
+// 2 = (cy+1,cz), 3 = (cy,cz-1), 4 = (cy,cz+1), 5 = (cy-1,cz-1).  Slot kSeg of
+// P/pre is the first word of the next segment, so that a rank at bit p+1 of
+// the segment's last word is still a shared-memory lookup.
+struct EmitShared {
+    uint32_t P[kEmitWarps][6][kSeg + 1];
+    int32_t pre[kEmitWarps][6][kSeg + 1]; // points before the word, within its row
+    uint32_t F[kEmitWarps][6][kSeg];      // face planes of row 0
+    int32_t dpre[kEmitWarps][kSeg];       // stencil entries before the word, within the row
+    uint32_t Q[kEmitWarps][3][kSeg];      // X, Y, Z words of sample row (cy, cz)
+    int32_t qpre[kEmitWarps][kSeg];       // quads before the word, within the sample row
+    uint16_t list[kEmitWarps][kSeg * 32]; // compacted bit positions of the segment
+};
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_emit(const T *__restrict__ lab, Classifier c, Geometry g, ExtractScratch s,
-                                              MeshArrays m, double3 sp, double3 org, const DevTotals *tot)
+__global__ void __launch_bounds__(kEmitWarps * 32, 3) k_emit(const T *__restrict__ lab, Classifier c, Geometry g,
+                                                             ExtractScratch s, MeshArrays m, const DevTotals *tot)
 {
+    __shared__ EmitShared sh;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int64_t rc = (int64_t)blockIdx.x * kEmitWarps + wp;
+    if (rc >= g.Rc) return;
     // output sizes, to keep every store in bounds even if the counts were inconsistent
     const int64_t NP = tot->n_points, NQ = tot->n_quads, NS = tot->n_stencil;
-    const int lane = threadIdx.x & 31;
-    const int64_t rc = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (rc >= g.Rc) return;
-    const int64_t ny1 = g.ny + 1;
+    const int64_t ny1 = g.ny + 1, W = g.W, WS = g.WS;
     const int64_t cy = rc % ny1 - 1, cz = rc / ny1 - 1;
-    const int64_t W = g.W;
     const bool has_srow = cy >= 0 && cz >= 0;
     const int64_t rs = has_srow ? cy + g.ny * cz : -1;
     const int np_row = s.cntP[rc];
     const int nq_row = has_srow ? s.cntQ[rs] : 0;
     if (np_row == 0 && nq_row == 0) return; // trimmed row
 
-    if (np_row > 0) {
-        const int64_t ra = sample_row(g, cy, cz), rb = sample_row(g, cy + 1, cz),
-                      rcc = sample_row(g, cy, cz + 1), rd = sample_row(g, cy + 1, cz + 1);
-        const int64_t base_p = s.offP[rc];
-        int64_t run_s = s.offS[rc];
-        const int64_t nb_row[6] = {-1, -1, rc - 1, rc + 1, rc - ny1, rc + ny1};
-        for (int64_t w0 = 0; w0 < W; w0 += 32) {
-            const int64_t w = w0 + lane;
-            Faces F;
-            uint32_t pw = 0;
-            int deg = 0;
-            if (w < W) {
-                F = cell_faces(s, g, ra, rb, rcc, rd, w);
+    int64_t rows[6];
+    rows[0] = rc;
+    rows[1] = cy >= 0 ? rc - 1 : -1;
+    rows[2] = cy + 1 < g.ny ? rc + 1 : -1;
+    rows[3] = cz >= 0 ? rc - ny1 : -1;
+    rows[4] = cz + 1 < g.nz ? rc + ny1 : -1;
+    rows[5] = (cy >= 0 && cz >= 0) ? rc - 1 - ny1 : -1;
+    int64_t base[6];
 #pragma unroll
-                for (int f = 0; f < 6; ++f) {
-                    pw |= F.f[f];
-                    deg += __popc(F.f[f]);
-                }
-            } else {
-#pragma unroll
-                for (int f = 0; f < 6; ++f) F.f[f] = 0u;
-            }
-            const int dincl = warp_incl_scan(deg, lane);
-            const int64_t sbase = run_s + dincl - deg;
-            uint32_t bits = pw;
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const uint32_t lt = (1u << b) - 1u;
-                const int64_t p = w * 32 + b;
-                const int32_t id = (int32_t)(base_p + s.preP[rc * W + w] + __popc(pw & lt));
-                if (id < 0 || id >= NP) continue;
-                const int64_t cx = p - 1;
-                float *pt = m.points + 3 * (int64_t)id;
-                pt[0] = centre_coord(org.x, sp.x, cx);
-                pt[1] = centre_coord(org.y, sp.y, cy);
-                pt[2] = centre_coord(org.z, sp.z, cz);
-                float *of = m.offsets + 3 * (int64_t)id;
-                of[0] = 0.f;
-                of[1] = 0.f;
-                of[2] = 0.f;
-                m.cells[id] = (uint64_t)(cx + 1) | ((uint64_t)(cy + 1) << 21) | ((uint64_t)(cz + 1) << 42);
-                int64_t so = sbase;
-                uint32_t mask = 0;
-#pragma unroll
-                for (int f = 0; f < 6; ++f) {
-                    so += __popc(F.f[f] & lt);
-                    mask |= ((F.f[f] >> b) & 1u) << f;
-                }
-                m.face_mask[id] = (uint8_t)mask;
-                m.sten_off[id] = so;
-                if (so < 0 || so > NS) continue;
-#pragma unroll
-                for (int f = 0; f < 6; ++f) {
-                    if (!((mask >> f) & 1u)) continue;
-                    int32_t nb;
-                    if (f == 0) nb = id - 1;
-                    else if (f == 1) nb = id + 1;
-                    else nb = rank_in_row(s, W, nb_row[f], p);
-                    if (so >= 0 && so < NS) m.sten_ids[so] = nb;
-                    ++so;
-                }
-            }
-            run_s += warp_sum(deg);
-        }
-    }
+    for (int r = 0; r < 6; ++r) base[r] = rows[r] >= 0 ? s.offP[rows[r]] : 0;
+    const int64_t ra = sample_row(g, cy, cz), rb = sample_row(g, cy + 1, cz), rcc = sample_row(g, cy, cz + 1),
+                  rd = sample_row(g, cy + 1, cz + 1);
+    const int64_t sbase = s.offS[rc];
+    const int64_t qbase = has_srow ? s.offQ[rs] : 0;
+    const T *srow = lab + (has_srow ? rs : 0) * g.nx;
+    int run[6] = {0, 0, 0, 0, 0, 0};
+    int srun = 0, qrun = 0;
+    int32_t reach = 1; // largest |neighbour id - id| seen by this lane (the -x/+x neighbours are 1 away)
+    uint32_t carry[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
-    if (nq_row > 0) {
-        const int64_t r00 = rc, rm0 = rc - 1, r0m = rc - ny1, rmm = rc - 1 - ny1;
-        const int64_t nx = g.nx;
-        const T *row = lab + rs * nx;
-        int64_t run_q = s.offQ[rs];
-        for (int64_t w0 = 0; w0 < W; w0 += 32) {
-            const int64_t w = w0 + lane;
-            const uint32_t xw = ldw(s.X, rs, w, W), yw = ldw(s.Y, rs, w, W), zw = ldw(s.Z, rs, w, W);
-            const int cntw = __popc(xw) + __popc(yw) + __popc(zw);
-            const int qincl = warp_incl_scan(cntw, lane);
-            const int64_t qbase = run_q + qincl - cntw;
-            uint32_t bits = xw | yw | zw;
+    for (int64_t w0 = 0; w0 < W; w0 += kSeg) {
+        const int64_t w = w0 + lane;
+        const bool valid = w < W;
+        int local0 = 0, seg0 = 0;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            const uint32_t pw = (valid && rows[r] >= 0) ? s.P[rows[r] * WS + w] : 0u;
+            const int pc = __popc(pw);
+            const int incl = warp_incl_scan(pc, lane);
+            const int segtot = __shfl_sync(kFull, incl, 31);
+            sh.P[wp][r][lane] = pw;
+            sh.pre[wp][r][lane] = run[r] + incl - pc;
+            if (r == 0) {
+                local0 = incl - pc;
+                seg0 = segtot;
+            }
+            run[r] += segtot;
+            if (lane == 0) {
+                const int64_t wn = w0 + kSeg;
+                sh.P[wp][r][kSeg] = (wn < W && rows[r] >= 0) ? s.P[rows[r] * WS + wn] : 0u;
+                sh.pre[wp][r][kSeg] = run[r];
+            }
+        }
+        // edge words of the four sample rows around the cell row, and of the previous word
+        uint32_t v[8] = {ldw(s.X, ra, w, W, WS), ldw(s.X, rb, w, W, WS), ldw(s.X, rcc, w, W, WS),
+                         ldw(s.X, rd, w, W, WS),  ldw(s.Y, ra, w, W, WS), ldw(s.Y, rcc, w, W, WS),
+                         ldw(s.Z, ra, w, W, WS),  ldw(s.Z, rb, w, W, WS)};
+        uint32_t pv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            pv[q] = __shfl_up_sync(kFull, v[q], 1);
+            if (lane == 0) pv[q] = carry[q];
+            carry[q] = __shfl_sync(kFull, v[q], 31);
+        }
+        const uint32_t Xa = v[0], Xb = v[1], Xc = v[2], Xd = v[3], Ya = v[4], Yc = v[5], Za = v[6], Zb = v[7];
+        uint32_t F[6];
+        F[0] = shl1(Ya | Yc | Za | Zb, pv[4] | pv[5] | pv[6] | pv[7]);
+        F[1] = Ya | Yc | Za | Zb;
+        F[2] = shl1(Xa | Xc | Za, pv[0] | pv[2] | pv[6]) | Za;
+        F[3] = shl1(Xb | Xd | Zb, pv[1] | pv[3] | pv[7]) | Zb;
+        F[4] = shl1(Xa | Xb | Ya, pv[0] | pv[1] | pv[4]) | Ya;
+        F[5] = shl1(Xc | Xd | Yc, pv[2] | pv[3] | pv[5]) | Yc;
+        int deg = 0;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            sh.F[wp][f][lane] = F[f];
+            deg += __popc(F[f]);
+        }
+        const int dincl = warp_incl_scan(deg, lane);
+        sh.dpre[wp][lane] = srun + dincl - deg;
+        srun += __shfl_sync(kFull, dincl, 31);
+        const int qc = __popc(Xa) + __popc(Ya) + __popc(Za);
+        const int qincl = warp_incl_scan(qc, lane);
+        sh.qpre[wp][lane] = qrun + qincl - qc;
+        qrun += __shfl_sync(kFull, qincl, 31);
+        sh.Q[wp][0][lane] = Xa;
+        sh.Q[wp][1][lane] = Ya;
+        sh.Q[wp][2][lane] = Za;
+
+        // ---- points and stencils of this segment
+        {
+            uint32_t bits = sh.P[wp][0][lane];
+            int k = local0;
             while (bits) {
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
+                sh.list[wp][k++] = (uint16_t)(lane * 32 + b);
+            }
+        }
+        __syncwarp();
+        for (int k = lane; k < seg0; k += 32) {
+            const int pos = sh.list[wp][k];
+            const int wl = pos >> 5, b = pos & 31;
+            const uint32_t lt = (1u << b) - 1u;
+            const int64_t id64 = base[0] + sh.pre[wp][0][wl] + __popc(sh.P[wp][0][wl] & lt);
+            if (id64 < 0 || id64 >= NP) continue;
+            const int32_t id = (int32_t)id64;
+            const int64_t cx = (w0 + wl) * 32 + b - 1;
+            float *pt = m.points + 3 * id64;
+            pt[0] = m.lut_x[cx + 1].x;
+            pt[1] = m.lut_y[cy + 1].x;
+            pt[2] = m.lut_z[cz + 1].x;
+            float *of = m.offsets + 3 * id64;
+            of[0] = 0.f;
+            of[1] = 0.f;
+            of[2] = 0.f;
+            m.cells[id] = (uint64_t)(cx + 1) | ((uint64_t)(cy + 1) << 21) | ((uint64_t)(cz + 1) << 42);
+            uint32_t mask = 0;
+            int64_t so = sbase + sh.dpre[wp][wl];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                const uint32_t fw = sh.F[wp][f][wl];
+                so += __popc(fw & lt);
+                mask |= ((fw >> b) & 1u) << f;
+            }
+            m.face_mask[id] = (uint8_t)mask;
+            m.sten_off[id] = so;
+            if (so < 0 || so + __popc(mask) > NS) continue;
+            int32_t *dst = m.sten_ids + so;
+            if (mask & 1u) *dst++ = id - 1;
+            if (mask & 2u) *dst++ = id + 1;
+            uint32_t dist[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int f = 2; f < 6; ++f)
+                if ((mask >> f) & 1u) {
+                    const int32_t nb =
+                        (int32_t)(base[f - 1] + sh.pre[wp][f - 1][wl] + __popc(sh.P[wp][f - 1][wl] & lt));
+                    *dst++ = nb;
+                    const int32_t d = nb > id ? nb - id : id - nb;
+                    reach = d > reach ? d : reach;
+                    dist[f - 2] = (uint32_t)d & 0x7fffu;
+                }
+            m.nbr[id] = make_uint2(dist[0] | ((mask & 1u) << 15) | (dist[1] << 16) | (((mask >> 1) & 1u) << 31),
+                                   dist[2] | (dist[3] << 16));
+        }
+        __syncwarp();
+
+        // ---- quads of sample row (cy, cz) in this segment
+        if (has_srow) {
+            const uint32_t any = Xa | Ya | Za;
+            const int pc = __popc(any);
+            const int incl = warp_incl_scan(pc, lane);
+            const int nseg = __shfl_sync(kFull, incl, 31);
+            uint32_t bits = any;
+            int k = incl - pc;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                sh.list[wp][k++] = (uint16_t)(lane * 32 + b);
+            }
+            __syncwarp();
+            for (int k2 = lane; k2 < nseg; k2 += 32) {
+                const int pos = sh.list[wp][k2];
+                const int wl = pos >> 5, b = pos & 31;
                 const uint32_t lt = (1u << b) - 1u;
-                const int64_t i = w * 32 + b;
-                int64_t q = qbase + __popc(xw & lt) + __popc(yw & lt) + __popc(zw & lt);
-                if (q < 0 || q + __popc(((xw >> b) & 1u) | (((yw >> b) & 1u) << 1) | (((zw >> b) & 1u) << 2)) > NQ)
-                    continue;
-                const uint32_t s0 = kappa<MODE>(c, ldlab(row, i));
-                if ((xw >> b) & 1u) {
-                    int4 v = make_int4(rank_in_row(s, W, rmm, i + 1), rank_in_row(s, W, r0m, i + 1),
-                                       rank_in_row(s, W, r00, i + 1), rank_in_row(s, W, rm0, i + 1));
-                    reinterpret_cast<int4 *>(m.quads)[q] = v;
-                    T *ql = reinterpret_cast<T *>(m.quad_labels) + 2 * q;
+                const uint32_t xw = sh.Q[wp][0][wl], yw = sh.Q[wp][1][wl], zw = sh.Q[wp][2][wl];
+                int64_t q = qbase + sh.qpre[wp][wl] + __popc(xw & lt) + __popc(yw & lt) + __popc(zw & lt);
+                const uint32_t hx = (xw >> b) & 1u, hy = (yw >> b) & 1u, hz = (zw >> b) & 1u;
+                if (q < 0 || q + (int64_t)(hx + hy + hz) > NQ) continue;
+                const int64_t i = (w0 + wl) * 32 + b;
+                // rank of cell bit (pos + d) in staged row r, d in {0, 1}
+                auto rk = [&](int r, int d) -> int32_t {
+                    const int pp = pos + d;
+                    const int ww = pp >> 5;
+                    const uint32_t l2 = (1u << (pp & 31)) - 1u;
+                    return (int32_t)(base[r] + sh.pre[wp][r][ww] + __popc(sh.P[wp][r][ww] & l2));
+                };
+                const uint32_t s0 = kappa<MODE>(c, ldlab(srow, i));
+                T *ql = reinterpret_cast<T *>(m.quad_labels) + 2 * q;
+                int4 *qd = reinterpret_cast<int4 *>(m.quads) + q;
+                if (hx) {
+                    const uint32_t s1 = kappa<MODE>(c, ldlab(srow, i + 1));
+                    *qd++ = make_int4(rk(5, 1), rk(3, 1), rk(0, 1), rk(1, 1));
                     ql[0] = (T)s0;
-                    ql[1] = (T)kappa<MODE>(c, ldlab(row, i + 1));
-                    ++q;
+                    ql[1] = (T)s1;
+                    ql += 2;
                 }
-                if ((yw >> b) & 1u) {
-                    int4 v = make_int4(rank_in_row(s, W, r0m, i), rank_in_row(s, W, r00, i),
-                                       rank_in_row(s, W, r00, i + 1), rank_in_row(s, W, r0m, i + 1));
-                    reinterpret_cast<int4 *>(m.quads)[q] = v;
-                    T *ql = reinterpret_cast<T *>(m.quad_labels) + 2 * q;
+                if (hy) {
+                    const uint32_t s1 = kappa<MODE>(c, ldlab(srow, i + g.nx));
+                    *qd++ = make_int4(rk(3, 0), rk(0, 0), rk(0, 1), rk(3, 1));
                     ql[0] = (T)s0;
-                    ql[1] = (T)kappa<MODE>(c, ldlab(row, i + nx));
-                    ++q;
+                    ql[1] = (T)s1;
+                    ql += 2;
                 }
-                if ((zw >> b) & 1u) {
-                    int4 v = make_int4(rank_in_row(s, W, rm0, i), rank_in_row(s, W, rm0, i + 1),
-                                       rank_in_row(s, W, r00, i + 1), rank_in_row(s, W, r00, i));
-                    reinterpret_cast<int4 *>(m.quads)[q] = v;
-                    T *ql = reinterpret_cast<T *>(m.quad_labels) + 2 * q;
+                if (hz) {
+                    const uint32_t s1 = kappa<MODE>(c, ldlab(srow, i + g.nx * g.ny));
+                    *qd = make_int4(rk(1, 0), rk(1, 1), rk(0, 1), rk(0, 0));
                     ql[0] = (T)s0;
-                    ql[1] = (T)kappa<MODE>(c, ldlab(row, i + nx * g.ny));
-                    ++q;
+                    ql[1] = (T)s1;
                 }
             }
-            run_q += __shfl_sync(kFull, qincl, 31);
+            __syncwarp();
         }
     }
+    reach = (int32_t)__reduce_max_sync(kFull, (unsigned)reach);
+    if (lane == 0) atomicMax(m.meta, reach);
 }
 
 template <typename T, int MODE>
@@ -495,10 +822,10 @@ cudaError_t planes_t(const void *labels, const Classifier &c, const Geometry &g,
 
 template <typename T, int MODE>
 cudaError_t emit_t(const void *labels, const Classifier &c, const Geometry &g, const ExtractScratch &s,
-                   const MeshArrays &m, double3 sp, double3 org, const DevTotals *tot, cudaStream_t st)
+                   const MeshArrays &m, const DevTotals *tot, cudaStream_t st)
 {
-    const int64_t blocks = (g.Rc + 7) / 8;
-    k_emit<T, MODE><<<(unsigned)blocks, 256, 0, st>>>((const T *)labels, c, g, s, m, sp, org, tot);
+    const int64_t blocks = (g.Rc + kEmitWarps - 1) / kEmitWarps;
+    k_emit<T, MODE><<<(unsigned)blocks, kEmitWarps * 32, 0, st>>>((const T *)labels, c, g, s, m, tot);
     return cudaGetLastError();
 }
 
@@ -513,14 +840,127 @@ cudaError_t planes_m(int type, const void *labels, const Classifier &c, const Ge
 
 template <int MODE>
 cudaError_t emit_m(int type, const void *labels, const Classifier &c, const Geometry &g, const ExtractScratch &s,
-                   const MeshArrays &m, double3 sp, double3 org, const DevTotals *tot, cudaStream_t st)
+                   const MeshArrays &m, const DevTotals *tot, cudaStream_t st)
 {
-    if (type == SN_U8) return emit_t<uint8_t, MODE>(labels, c, g, s, m, sp, org, tot, st);
-    if (type == SN_U16) return emit_t<uint16_t, MODE>(labels, c, g, s, m, sp, org, tot, st);
-    return emit_t<uint32_t, MODE>(labels, c, g, s, m, sp, org, tot, st);
+    if (type == SN_U8) return emit_t<uint8_t, MODE>(labels, c, g, s, m, tot, st);
+    if (type == SN_U16) return emit_t<uint16_t, MODE>(labels, c, g, s, m, tot, st);
+    return emit_t<uint32_t, MODE>(labels, c, g, s, m, tot, st);
+}
+
+
+template <typename T, int MODE, bool FAST>
+cudaError_t count_f(const void *labels, const Classifier &c, const Geometry &g, const ExtractScratch &s,
+                    const CountTiling &tl, size_t smem, DevTotals *tot, cudaStream_t st)
+{
+    cudaError_t e =
+        cudaFuncSetAttribute(k_count<T, MODE, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((g.ny + tl.ty - 1) / tl.ty), (unsigned)((g.nz + tl.kz - 1) / tl.kz));
+    k_count<T, MODE, FAST><<<grid, 256, smem, st>>>((const T *)labels, c, g, s, tl, tot);
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+cudaError_t count_t(const void *labels, const Classifier &c, const Geometry &g, const ExtractScratch &s,
+                    const CountTiling &tl, size_t smem, DevTotals *tot, cudaStream_t st)
+{
+    // packed compares need every value to be its own class and 16-byte aligned rows
+    if constexpr (MODE == CLASS_ALL) {
+        if (tl.aligned) return count_f<T, MODE, true>(labels, c, g, s, tl, smem, tot, st);
+    }
+    return count_f<T, MODE, false>(labels, c, g, s, tl, smem, tot, st);
+}
+
+template <int MODE>
+cudaError_t count_m(int type, const void *labels, const Classifier &c, const Geometry &g, const ExtractScratch &s,
+                    const CountTiling &tl, size_t smem, DevTotals *tot, cudaStream_t st)
+{
+    if (type == SN_U8) return count_t<uint8_t, MODE>(labels, c, g, s, tl, smem, tot, st);
+    if (type == SN_U16) return count_t<uint16_t, MODE>(labels, c, g, s, tl, smem, tot, st);
+    return count_t<uint32_t, MODE>(labels, c, g, s, tl, smem, tot, st);
+}
+
+// Cell-centre coordinate origin + spacing * (c + 1/2) for c = -1..n-1 on each
+// axis, computed in FP64 with the product and the sum each rounded once, then
+// split into the nearest float (hi) and the float nearest to the remainder (lo).
+__global__ void k_centre_lut(float2 *lut, int64_t nx, int64_t ny, int64_t nz, double3 sp, double3 org)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = nx + ny + nz + 3;
+    if (k >= total) return;
+    int64_t c;
+    double s, o;
+    if (k < nx + 1) {
+        c = k - 1;
+        s = sp.x;
+        o = org.x;
+    } else if (k < nx + ny + 2) {
+        c = k - (nx + 1) - 1;
+        s = sp.y;
+        o = org.y;
+    } else {
+        c = k - (nx + ny + 2) - 1;
+        s = sp.z;
+        o = org.z;
+    }
+    const double v = __dadd_rn(o, __dmul_rn(s, (double)c + 0.5));
+    const float hi = __double2float_rn(v);
+    lut[k] = make_float2(hi, __double2float_rn(__dsub_rn(v, (double)hi)));
 }
 
 } // namespace
+
+cudaError_t launch_centre_lut(const MeshArrays &m, const int64_t dims[3], const double spacing[3],
+                              const double origin[3], cudaStream_t st)
+{
+    const int64_t total = dims[0] + dims[1] + dims[2] + 3;
+    k_centre_lut<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+        m.lut_x, dims[0], dims[1], dims[2], make_double3(spacing[0], spacing[1], spacing[2]),
+        make_double3(origin[0], origin[1], origin[2]));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count(int type, const void *labels, const Classifier &c, const Geometry &g,
+                         const ExtractScratch &s, DevTotals *tot, cudaStream_t st)
+{
+    const int64_t row_bytes = g.nx * (int64_t)type;
+    constexpr int64_t kSlotBudget = 24 * 1024; // bytes of labels per slot
+    // rows per tile: fit the slot budget, and make the (rows + 1) * W edge-word
+    // items of a slice fill the 256 threads as evenly as possible
+    int ty = 0;
+    double best = -1.0;
+    for (int t = 1; t <= kCountMaxTY; ++t) {
+        if ((t + 1) * row_bytes > kSlotBudget) break;
+        const int64_t items = (int64_t)(t + 1) * g.W;
+        const double fill = (double)(t * g.W) / (double)(((items + 255) / 256) * 256);
+        if (fill > best + 1e-9) {
+            best = fill;
+            ty = t;
+        }
+    }
+    if (ty == 0 || g.W > 4096) return cudaErrorNotSupported;
+    CountTiling tl;
+    tl.ty = ty;
+    tl.W = (int)g.W;
+    tl.wdiv = (0x100000000ull + (uint64_t)g.W - 1) / (uint64_t)g.W;
+    tl.slot_bytes = (int)((((ty + 1) * row_bytes) + 127) / 128 * 128);
+    tl.aligned = (row_bytes % 16 == 0) && ((reinterpret_cast<uintptr_t>(labels) & 15) == 0);
+    // enough z-tiles to fill the GPU about twice over, slices per tile in [4, 64]
+    const int64_t ytiles = (g.ny + ty - 1) / ty;
+    int64_t kz = (g.nz * ytiles + 2 * 152 * 4 - 1) / (2 * 152 * 4);
+    if (kz < 4) kz = 4;
+    if (kz > 64) kz = 64;
+    tl.kz = (int)kz;
+    // + 256: the packed compares read up to 33 samples past a row's last word
+    const size_t smem = kCountHeader + (size_t)kCountSlots * tl.slot_bytes + 2 * 3 * (size_t)(ty + 1) * g.W * 4 + 256;
+    if (smem > 200 * 1024) return cudaErrorNotSupported;
+    cudaError_t e = cudaMemsetAsync(s.cntQ, 0, sizeof(int32_t) * (size_t)g.Rc, st);
+    if (e != cudaSuccess) return e;
+    ProfScope ps("k_count", st);
+    if (c.mode == CLASS_ALL) return count_m<CLASS_ALL>(type, labels, c, g, s, tl, smem, tot, st);
+    if (c.mode == CLASS_BITMAP) return count_m<CLASS_BITMAP>(type, labels, c, g, s, tl, smem, tot, st);
+    return count_m<CLASS_SORTED>(type, labels, c, g, s, tl, smem, tot, st);
+}
 
 cudaError_t launch_planes(int type, const void *labels, const Classifier &c, const Geometry &g,
                           const ExtractScratch &s, cudaStream_t st)
@@ -546,23 +986,18 @@ cudaError_t launch_scan(const Geometry &g, const ExtractScratch &s, DevTotals *t
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(s.scan_ticket, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(totals, 0, sizeof(DevTotals), st);
-    if (e != cudaSuccess) return e;
     ProfScope ps("k_scan", st);
     k_scan<<<ntiles, kScanThreads, 0, st>>>(g, s, totals, ntiles);
     return cudaGetLastError();
 }
 
 cudaError_t launch_emit(int type, const void *labels, const Classifier &c, const Geometry &g,
-                        const ExtractScratch &s, const MeshArrays &m, const double spacing[3],
-                        const double origin[3], const DevTotals *tot, cudaStream_t st)
+                        const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st)
 {
     ProfScope ps("k_emit", st);
-    const double3 sp = make_double3(spacing[0], spacing[1], spacing[2]);
-    const double3 org = make_double3(origin[0], origin[1], origin[2]);
-    if (c.mode == CLASS_ALL) return emit_m<CLASS_ALL>(type, labels, c, g, s, m, sp, org, tot, st);
-    if (c.mode == CLASS_BITMAP) return emit_m<CLASS_BITMAP>(type, labels, c, g, s, m, sp, org, tot, st);
-    return emit_m<CLASS_SORTED>(type, labels, c, g, s, m, sp, org, tot, st);
+    if (c.mode == CLASS_ALL) return emit_m<CLASS_ALL>(type, labels, c, g, s, m, tot, st);
+    if (c.mode == CLASS_BITMAP) return emit_m<CLASS_BITMAP>(type, labels, c, g, s, m, tot, st);
+    return emit_m<CLASS_SORTED>(type, labels, c, g, s, m, tot, st);
 }
 
 } // namespace sn

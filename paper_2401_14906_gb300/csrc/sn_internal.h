@@ -3,8 +3,9 @@
 // Data layout in device memory (x fastest everywhere):
 //   sample row rs = j + ny*k            (ny*nz rows of the label map)
 //   cell row   rc = (cy+1) + (ny+1)*(cz+1), cy in [-1,ny-1], cz in [-1,nz-1]
-//   every row is W = ceil((nx+1)/32) 32-bit words; bit p of a cell row is the
-//   cell cx = p-1, bit i of a sample row is the sample i.
+//   every row is W = ceil((nx+1)/32) 32-bit words, stored with a stride of WS =
+//   W rounded up to 4 words (16 bytes, so runs of rows can be bulk-copied); bit
+//   p of a cell row is the cell cx = p-1, bit i of a sample row is the sample i.
 //   X/Y/Z planes: bit i of row rs is set iff the x/y/z edge from sample (i,j,k)
 //   is intersected (Sec. 2.2 edge test; Sec. 2.3 Passes 1-2 "triads" as bit
 //   planes).  P plane: bit p of row rc is set iff cell (p-1,cy,cz) has a point.
@@ -35,15 +36,15 @@ struct Classifier {
 struct Geometry {
     int64_t nx, ny, nz;
     int64_t W;  // words per row
+    int64_t WS; // row stride in words (W rounded up to a multiple of 4)
     int64_t Rs; // sample rows ny*nz
     int64_t Rc; // cell rows (ny+1)*(nz+1)
 };
 
 // Device temporaries of one extraction.
 struct ExtractScratch {
-    uint32_t *X, *Y, *Z;  // [Rs][W]
-    uint32_t *P;          // [Rc][W]
-    int32_t *preP;        // [Rc][W] exclusive popcount of P before each word, within the row
+    uint32_t *X, *Y, *Z;  // [Rs][WS]
+    uint32_t *P;          // [Rc][WS]
     int32_t *cntP;        // [Rc] points per cell row
     int32_t *cntS;        // [Rc] stencil entries per cell row
     int32_t *cntQ;        // [Rc] quads per sample row rs (entries rs >= Rs are 0)
@@ -56,7 +57,7 @@ struct ExtractScratch {
 // Totals read back by the host after the scan.
 struct DevTotals {
     int64_t n_points, n_stencil, n_quads;
-    int32_t error; // bit 0: look-back spin limit hit
+    int32_t error; // bit 0: look-back spin limit hit, bit 1: a label copy wait gave up
     int32_t pad;
 };
 
@@ -70,7 +71,15 @@ struct MeshArrays {
     int64_t *sten_off;   // [np+1]
     int32_t *sten_ids;   // [ns]
     uint8_t *face_mask;  // [np]
+    int32_t *meta;       // [4]: 0 = max |neighbour id - id| over all stencils, 1 = smoothing error flag
+    float2 *lut_x, *lut_y, *lut_z; // [n+1] cell-centre world coordinate per axis for c = -1..n-1, as
+                                   // (hi, lo): hi = the coordinate rounded to float, lo = the rest
+    uint2 *nbr;          // [np] packed neighbour record for the smoothing sweeps (valid while meta[0] < 2^15):
+                         //   .x = d(-y) | d(+y) << 16, .y = d(-z) | d(+z) << 16, each 15-bit |id distance|,
+                         //   0 = no neighbour; bit 15 of the -y / +y fields = -x / +x neighbour present
 };
+
+constexpr int32_t kPackedReach = 1 << 15; // packed records hold id distances below this
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
@@ -81,16 +90,27 @@ constexpr int kSpinLimit = 1 << 22;
 cudaError_t launch_planes(int type, const void *labels, const Classifier &c, const Geometry &g,
                           const ExtractScratch &s, cudaStream_t st);
 cudaError_t launch_cellrows(const Geometry &g, const ExtractScratch &s, cudaStream_t st);
+// Passes 1-3 counting in one streaming kernel; returns cudaErrorNotSupported when
+// a tile of rows does not fit shared memory (the two kernels above are used then).
+cudaError_t launch_count(int type, const void *labels, const Classifier &c, const Geometry &g,
+                         const ExtractScratch &s, DevTotals *tot, cudaStream_t st);
 cudaError_t launch_scan(const Geometry &g, const ExtractScratch &s, DevTotals *totals, cudaStream_t st);
 cudaError_t launch_emit(int type, const void *labels, const Classifier &c, const Geometry &g,
-                        const ExtractScratch &s, const MeshArrays &m, const double spacing[3],
-                        const double origin[3], const DevTotals *tot, cudaStream_t st);
+                        const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st);
+
+// Pass 4 over tiles of cell rows (sn_emit.cu); cudaErrorNotSupported for rows too
+// wide for its shared-memory staging (launch_emit is used then).
+cudaError_t launch_emit_tile(int type, const void *labels, const Classifier &c, const Geometry &g,
+                             const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st);
+
+// per-axis cell-centre tables of a mesh (sn_extract.cu)
+cudaError_t launch_centre_lut(const MeshArrays &m, const int64_t dims[3], const double spacing[3],
+                              const double origin[3], cudaStream_t st);
 
 // launchers (sn_smooth.cu)
 cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float relaxation, float half,
-                          float *scratch, const double spacing[3], const double origin[3], cudaStream_t st);
-cudaError_t launch_centres(const MeshArrays &m, int64_t np, const double spacing[3], const double origin[3],
-                           cudaStream_t st);
+                          float *scratch, const double spacing[3], cudaStream_t st);
+cudaError_t launch_centres(const MeshArrays &m, int64_t np, cudaStream_t st);
 
 // detail message returned by sn_last_error() on this thread (sn_api.cu)
 void set_last_error(const char *msg);

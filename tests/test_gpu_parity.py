@@ -85,6 +85,23 @@ def test_degenerate_and_empty():
     parity(((x + y + z) % 2).astype(np.uint8), iterations=5)
 
 
+def test_wide_slices_use_the_stencil_fallback():
+    # a checkerboard with 261x261 cells per slice: -z/+z neighbours are ~68k ids
+    # apart, beyond the 15-bit packed neighbour record, so the sweeps read the CSR
+    z, y, x = np.mgrid[0:3, 0:260, 0:260]
+    parity(((x + y + z) % 2).astype(np.uint8), iterations=6)
+    # and a map just below the limit in the same run of tests
+    z, y, x = np.mgrid[0:3, 0:150, 0:150]
+    parity(((x + y + z) % 2).astype(np.uint8), iterations=6)
+
+
+def test_very_wide_rows_use_the_per_row_kernels():
+    # 3100 uint32 labels per row (12.4 KB) do not fit the shared-memory row tile
+    rng = np.random.default_rng(77)
+    lab = rng.integers(0, 3, size=(3, 4, 3100)).astype(np.uint32)
+    parity(lab, iterations=4)
+
+
 def test_host_labels_are_copied():
     lab = sn_synth.ellipsoids((50, 40, 30), 5, 4.0, 12.0, np.uint16, seed=6)
     parity(lab, iterations=8, on_device=False)
