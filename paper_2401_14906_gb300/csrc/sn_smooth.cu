@@ -37,7 +37,7 @@ struct SweepArgs {
     int64_t np;
     float lam, h;
     float spx, spy, spz;
-    int last;
+    int first, last; // first sweep: offsets are all zero; last sweep: also write world coordinates
 };
 
 // world coordinate of a cell centre (hi, lo) displaced by spacing * o
@@ -65,13 +65,15 @@ __device__ __forceinline__ void sweep_point(const SweepArgs &a, uint32_t i, floa
     const int n = (int)(mx + px + (dmy != 0) + (dpy != 0) + (dmz != 0) + (dpz != 0));
     float3 acc = make_float3((float)((int)px - (int)mx), (float)((int)(dpy != 0) - (int)(dmy != 0)),
                              (float)((int)(dpz != 0) - (int)(dmz != 0)));
-    // neighbours in face order -x, +x, -y, +y, -z, +z
-    if (mx) add_diff(acc, ld3(oin, i - 1), o);
-    if (px) add_diff(acc, ld3(oin, i + 1), o);
-    if (dmy) add_diff(acc, ld3(oin, i - dmy), o);
-    if (dpy) add_diff(acc, ld3(oin, i + dpy), o);
-    if (dmz) add_diff(acc, ld3(oin, i - dmz), o);
-    if (dpz) add_diff(acc, ld3(oin, i + dpz), o);
+    // neighbours in face order -x, +x, -y, +y, -z, +z (all offsets are zero before the first sweep)
+    if (!a.first) {
+        if (mx) add_diff(acc, ld3(oin, i - 1), o);
+        if (px) add_diff(acc, ld3(oin, i + 1), o);
+        if (dmy) add_diff(acc, ld3(oin, i - dmy), o);
+        if (dpy) add_diff(acc, ld3(oin, i + dpy), o);
+        if (dmz) add_diff(acc, ld3(oin, i - dmz), o);
+        if (dpz) add_diff(acc, ld3(oin, i + dpz), o);
+    }
     const float ln = a.lam * kInv[n];
     const float nx = fminf(fmaxf(o.x + ln * acc.x, -a.h), a.h);
     const float ny = fminf(fmaxf(o.y + ln * acc.y, -a.h), a.h);
@@ -94,14 +96,14 @@ __device__ __forceinline__ void sweep_point(const SweepArgs &a, uint32_t i, floa
 __device__ __forceinline__ void sweep_point_csr(const SweepArgs &a, uint32_t i)
 {
     const float *__restrict__ oin = a.oin;
-    const float3 o = ld3(oin, i);
+    const float3 o = a.first ? make_float3(0.f, 0.f, 0.f) : ld3(oin, i);
     const uint32_t m = a.fmask[i];
     const int64_t b = a.soff[i];
     const int n = __popc(m);
     float3 acc = make_float3((float)((int)((m >> 1) & 1u) - (int)(m & 1u)),
                              (float)((int)((m >> 3) & 1u) - (int)((m >> 2) & 1u)),
                              (float)((int)((m >> 5) & 1u) - (int)((m >> 4) & 1u)));
-    for (int t = 0; t < n; ++t) {
+    for (int t = 0; t < (a.first ? 0 : n); ++t) {
         const int64_t j = a.sids[b + t];
         if ((uint64_t)j >= (uint64_t)a.np) continue; // stencil ids are always < np
         add_diff(acc, ld3(oin, (uint32_t)j), o);
@@ -128,7 +130,8 @@ constexpr int kSweepThreads = 256, kSweepPoints = 2 * kSweepThreads; // two poin
 
 // One Jacobi sweep.  Each thread updates two points kSweepThreads apart; the
 // own offsets and neighbour records of both are loaded before either point's
-// neighbours are gathered, so that twice as many loads are in flight.
+// neighbours are gathered, so that twice as many loads are in flight.  The
+// first sweep starts from zero offsets and reads none.
 __global__ void __launch_bounds__(kSweepThreads) k_smooth(SweepArgs a)
 {
     const uint32_t i0 = blockIdx.x * (uint32_t)kSweepPoints + threadIdx.x, i1 = i0 + kSweepThreads;
@@ -142,11 +145,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_smooth(SweepArgs a)
     float3 o0 = make_float3(0.f, 0.f, 0.f), o1 = o0;
     uint2 r0 = make_uint2(0u, 0u), r1 = r0;
     if (h0) {
-        o0 = ld3(a.oin, i0);
+        if (!a.first) o0 = ld3(a.oin, i0);
         r0 = a.nbr[i0];
     }
     if (h1) {
-        o1 = ld3(a.oin, i1);
+        if (!a.first) o1 = ld3(a.oin, i1);
         r1 = a.nbr[i1];
     }
     if (h0) sweep_point(a, i0, o0, r0);
@@ -201,15 +204,15 @@ cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float
     a.spx = (float)spacing[0];
     a.spy = (float)spacing[1];
     a.spz = (float)spacing[2];
-    // pick the first source so that the last sweep writes m.offsets
+    // pick the first source so that the last sweep writes m.offsets (the first sweep reads no offsets)
     float *src = (iterations % 2 == 1) ? scratch : m.offsets;
     float *dst = (iterations % 2 == 1) ? m.offsets : scratch;
-    cudaError_t e = cudaMemsetAsync(src, 0, sizeof(float) * 3 * (size_t)np, st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
     const unsigned blocks = (unsigned)((np + kSweepPoints - 1) / kSweepPoints);
     for (int t = 0; t < iterations; ++t) {
         a.oin = src;
         a.oout = dst;
+        a.first = t == 0;
         a.last = t == iterations - 1;
         ProfScope ps("k_smooth", st);
         k_smooth<<<blocks, kSweepThreads, 0, st>>>(a);
