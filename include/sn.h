@@ -132,6 +132,43 @@ sn_status sn_smooth_static(const int64_t *stencil_offsets, const int32_t *stenci
                            int64_t n_points, int iterations, float relaxation, float constraint_distance,
                            float *offsets, void *cuda_stream);
 
+/*
+ * sn_smooth_ex -- sn_smooth with a choice of constraint (Sec. 2.2: the motion of
+ * a point is constrained "as a fraction of the hexahedral voxel cell, or more
+ * simply as a constraint sphere centered at the voxel center point").
+ *   SN_CONSTRAINT_BOX     |o_a| <= d/2 per axis (what sn_smooth does);
+ *   SN_CONSTRAINT_SPHERE  |o| <= d/2, o measured in voxel units (a ball around
+ *                         the cell centre; an ellipsoid in world units when the
+ *                         spacing is anisotropic); an update that leaves the ball
+ *                         is scaled back onto it.
+ * Other arguments and errors as for sn_smooth.
+ */
+typedef enum { SN_CONSTRAINT_BOX = 0, SN_CONSTRAINT_SPHERE = 1 } sn_constraint;
+sn_status sn_smooth_ex(sn_mesh *m, int iterations, float relaxation, float constraint_distance,
+                       sn_constraint constraint);
+
+/*
+ * sn_triangulate -- surface triangulation (Sec. 2.5): two triangles per quad,
+ * split along one diagonal of the quad's current points (smoothed or not).
+ *   SN_TRI_GREEDY     always the diagonal v0-v2;
+ *   SN_TRI_SHORTEST   the shorter diagonal (v0-v2 on a tie);
+ *   SN_TRI_MIN_AREA   the split with the smaller total triangle area;
+ *   SN_TRI_COPLANAR   the split whose two triangle normals are most nearly
+ *                     parallel (largest cosine between them).
+ * Quad (v0,v1,v2,v3) gives triangles 2q and 2q+1: (v0,v1,v2),(v0,v2,v3) for the
+ * v0-v2 diagonal or (v0,v1,v3),(v1,v2,v3) for v1-v3, keeping the quad's winding
+ * (normal along +axis).  Triangle t carries the labels of quad t/2.  Decisions
+ * are made in FP32 with unfused multiplies and adds, in the order documented in
+ * sn_triangulate.cu.  The triangles are owned by the mesh (int32 [2*nq][3],
+ * sn_mesh_triangles); a new call replaces them.  Enqueued on the mesh's stream.
+ * Errors: SN_EINVAL, SN_ENOMEM, SN_ECUDA.
+ */
+typedef enum { SN_TRI_GREEDY = 0, SN_TRI_SHORTEST = 1, SN_TRI_MIN_AREA = 2, SN_TRI_COPLANAR = 3 } sn_tri_method;
+sn_status sn_triangulate(sn_mesh *m, sn_tri_method method);
+
+/* Borrowed device pointer to the triangles (NULL before sn_triangulate). */
+sn_status sn_mesh_triangles(const sn_mesh *m, const int32_t **triangles);
+
 /* Output sizes: points, quads, stencil entries (sum of stencil lengths). */
 sn_status sn_mesh_counts(const sn_mesh *m, int64_t *n_points, int64_t *n_quads, int64_t *n_stencil);
 

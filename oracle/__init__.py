@@ -60,7 +60,10 @@ def _load():
             lib.or_extract.restype = ctypes.c_int
             lib.or_smooth.argtypes = [ctypes.POINTER(_OrMesh), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double,
-                                      ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+            lib.or_triangulate.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            lib.or_triangulate.restype = ctypes.c_int
             lib.or_smooth.restype = ctypes.c_int
             lib.or_free.argtypes = [ctypes.POINTER(_OrMesh)]
             lib.or_free.restype = None
@@ -117,8 +120,8 @@ def extract(labels: np.ndarray, spacing=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0),
 
 
 def smooth(mesh: OracleMesh, spacing=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0), iterations=16, relaxation=0.5,
-           constraint=1.0):
-    """Step 6 (Eq. 1, double-buffered, box-constrained).  Returns (offsets, points), FP64 (n, 3)."""
+           constraint=1.0, sphere=False):
+    """Step 6 (Eq. 1, double-buffered; box or sphere constraint).  Returns (offsets, points), FP64 (n, 3)."""
     lib = _load()
     m = _OrMesh()
     m.n_points, m.n_quads, m.n_stencil = mesh.n_points, mesh.n_quads, mesh.n_stencil
@@ -136,7 +139,29 @@ def smooth(mesh: OracleMesh, spacing=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0), it
     sp = (ctypes.c_double * 3)(*[float(s) for s in spacing])
     org = (ctypes.c_double * 3)(*[float(o) for o in origin])
     rc = lib.or_smooth(ctypes.byref(m), sp, org, int(iterations), float(relaxation), float(constraint),
-                       off.ctypes.data, pts.ctypes.data)
+                       1 if sphere else 0, off.ctypes.data, pts.ctypes.data)
     if rc != 0:
         raise RuntimeError(f"or_smooth failed with code {rc}")
     return off[:n], pts[:n]
+
+
+TRI_METHODS = {"greedy": 0, "shortest": 1, "min_area": 2, "coplanar": 3}
+
+
+def triangulate(points, quads, method="shortest"):
+    """Step 7 on float32 points (n, 3) and quads (q, 4).
+
+    Returns (triangles (2q, 3) int32, alt (q,) bool: split along v1-v3, metrics (q, 2) float32 compared)."""
+    lib = _load()
+    pts = np.ascontiguousarray(points, dtype=np.float32)
+    qd = np.ascontiguousarray(quads, dtype=np.int32)
+    nq = qd.shape[0]
+    tris = np.zeros((max(2 * nq, 1), 3), dtype=np.int32)
+    alt = np.zeros(max(nq, 1), dtype=np.uint8)
+    m02 = np.zeros(max(nq, 1), dtype=np.float32)
+    m13 = np.zeros(max(nq, 1), dtype=np.float32)
+    rc = lib.or_triangulate(pts.ctypes.data if pts.size else None, qd.ctypes.data if qd.size else None, nq,
+                            TRI_METHODS[method], tris.ctypes.data, alt.ctypes.data, m02.ctypes.data, m13.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"or_triangulate failed with code {rc}")
+    return tris[:2 * nq], alt[:nq].astype(bool), np.stack([m02[:nq], m13[:nq]], axis=1)

@@ -32,8 +32,13 @@
  *                       lambda times the mean of (p_j - p_i) over its stencil, then
  *                       is clamped to the box of half-width d/2 voxel around its
  *                       cell centre (Sec. 2.2, "constrained relative to its
- *                       generating voxel cell").
+ *                       generating voxel cell"), or projected onto the ball of
+ *                       radius d/2 voxel (the constraint sphere of Sec. 2.2);
+ *   7. triangulation    two triangles per quad along one diagonal (Sec. 2.5),
+ *                       chosen greedily, by the shorter diagonal, the smaller
+ *                       total area or the more co-planar pair of triangles.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -252,11 +257,13 @@ int or_extract(const void *labels, int type, const int64_t dims[3], const double
 
 /* Smoothing, step 6 (Eq. 1 with the double buffer of Sec. 2.4).  Works in
  * cell-local voxel units: o_i is the displacement of point i from its cell
- * centre and p_j - p_i = (c_j - c_i) + (o_j - o_i).  After `iterations` sweeps
- * offsets_out holds o (3 per point) and points_out the world positions
+ * centre and p_j - p_i = (c_j - c_i) + (o_j - o_i).  sphere = 0 clamps each
+ * component to [-d/2, d/2]; sphere = 1 scales the displacement back onto the
+ * ball |o| <= d/2 when it leaves it.  After `iterations` sweeps offsets_out
+ * holds o (3 per point) and points_out the world positions
  * origin + spacing * (c + 1/2 + o).  Either output may be NULL. */
 int or_smooth(const or_mesh *m, const double spacing[3], const double origin[3], int iterations,
-              double relaxation, double constraint, double *offsets_out, double *points_out)
+              double relaxation, double constraint, int sphere, double *offsets_out, double *points_out)
 {
     if (!m || !spacing || !origin || iterations < 0) return 1;
     int64_t np = m->n_points;
@@ -267,6 +274,7 @@ int or_smooth(const or_mesh *m, const double spacing[3], const double origin[3],
     for (int t = 0; t < iterations; ++t) {
         for (int64_t i = 0; i < np; ++i) {
             int64_t n = m->stencil_offsets[i + 1] - m->stencil_offsets[i];
+            double o[3];
             for (int c = 0; c < 3; ++c) {
                 double sum = 0.0;
                 for (int64_t s = m->stencil_offsets[i]; s < m->stencil_offsets[i + 1]; ++s) {
@@ -275,12 +283,20 @@ int or_smooth(const or_mesh *m, const double spacing[3], const double origin[3],
                     double pi = (double)m->cells[3 * i + c] + a[3 * i + c];
                     sum += pj - pi;
                 }
-                double o = a[3 * i + c];
-                if (n > 0) o = o + relaxation * (sum / (double)n);
-                if (o < -h) o = -h;
-                if (o > h) o = h;
-                b[3 * i + c] = o;
+                o[c] = a[3 * i + c];
+                if (n > 0) o[c] = o[c] + relaxation * (sum / (double)n);
             }
+            if (!sphere) {
+                for (int c = 0; c < 3; ++c) {
+                    if (o[c] < -h) o[c] = -h;
+                    if (o[c] > h) o[c] = h;
+                }
+            } else {
+                double r = sqrt(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]);
+                if (r > h)
+                    for (int c = 0; c < 3; ++c) o[c] = o[c] * (h / r);
+            }
+            for (int c = 0; c < 3; ++c) b[3 * i + c] = o[c];
         }
         double *tmp = a; a = b; b = tmp;
     }
@@ -292,5 +308,68 @@ int or_smooth(const or_mesh *m, const double spacing[3], const double origin[3],
                     origin[c] + spacing[c] * ((double)m->cells[3 * i + c] + 0.5 + a[3 * i + c]);
         }
     free(a); free(b);
+    return 0;
+}
+
+/* Triangulation, step 7, in single precision with every operation rounded on
+ * its own (this file is compiled without floating-point contraction):
+ *   sq(v) = (v.x*v.x + v.y*v.y) + v.z*v.z, |v| = sqrtf(sq(v)),
+ *   cross(u,v) = (u.y*v.z - u.z*v.y, u.z*v.x - u.x*v.z, u.x*v.y - u.y*v.x).
+ * method 0: diagonal v0-v2; 1: the shorter diagonal (sq(p3-p1) < sq(p2-p0)
+ * picks v1-v3); 2: the smaller sum of the two triangles' |cross|; 3: the larger
+ * cosine between the two triangles' normals.  alt[q] = 1 when the split is
+ * v1-v3; m02/m13 (optional) receive the two metric values compared. */
+typedef struct { float x, y, z; } or_v3;
+static or_v3 v3sub(or_v3 a, or_v3 b) { or_v3 r = {a.x - b.x, a.y - b.y, a.z - b.z}; return r; }
+static float v3dot(or_v3 a, or_v3 b) { float r = a.x * b.x; r = r + a.y * b.y; return r + a.z * b.z; }
+static or_v3 v3cross(or_v3 u, or_v3 v)
+{
+    or_v3 r = {u.y * v.z - u.z * v.y, u.z * v.x - u.x * v.z, u.x * v.y - u.y * v.x};
+    return r;
+}
+static float v3norm(or_v3 v) { return sqrtf(v3dot(v, v)); }
+
+int or_triangulate(const float *points, const int32_t *quads, int64_t nq, int method, int32_t *tris, uint8_t *alt,
+                   float *m02, float *m13)
+{
+    if ((!points && nq > 0) || (!quads && nq > 0) || !tris || method < 0 || method > 3) return 1;
+    for (int64_t q = 0; q < nq; ++q) {
+        const int32_t *v = quads + 4 * q;
+        or_v3 p[4];
+        for (int r = 0; r < 4; ++r) {
+            p[r].x = points[3 * (int64_t)v[r]];
+            p[r].y = points[3 * (int64_t)v[r] + 1];
+            p[r].z = points[3 * (int64_t)v[r] + 2];
+        }
+        float a = 0.f, b = 0.f;
+        int use13 = 0;
+        if (method == 1) {
+            or_v3 d02 = v3sub(p[2], p[0]), d13 = v3sub(p[3], p[1]);
+            a = v3dot(d02, d02);
+            b = v3dot(d13, d13);
+            use13 = b < a;
+        } else if (method == 2) {
+            a = v3norm(v3cross(v3sub(p[1], p[0]), v3sub(p[2], p[0]))) +
+                v3norm(v3cross(v3sub(p[2], p[0]), v3sub(p[3], p[0])));
+            b = v3norm(v3cross(v3sub(p[1], p[0]), v3sub(p[3], p[0]))) +
+                v3norm(v3cross(v3sub(p[2], p[1]), v3sub(p[3], p[1])));
+            use13 = b < a;
+        } else if (method == 3) {
+            or_v3 n0 = v3cross(v3sub(p[1], p[0]), v3sub(p[2], p[0])), n1 = v3cross(v3sub(p[2], p[0]), v3sub(p[3], p[0]));
+            or_v3 k0 = v3cross(v3sub(p[1], p[0]), v3sub(p[3], p[0])), k1 = v3cross(v3sub(p[2], p[1]), v3sub(p[3], p[1]));
+            a = v3dot(n0, n1) / (v3norm(n0) * v3norm(n1));
+            b = v3dot(k0, k1) / (v3norm(k0) * v3norm(k1));
+            use13 = b > a;
+        }
+        int32_t *t = tris + 6 * q;
+        if (!use13) {
+            t[0] = v[0]; t[1] = v[1]; t[2] = v[2]; t[3] = v[0]; t[4] = v[2]; t[5] = v[3];
+        } else {
+            t[0] = v[0]; t[1] = v[1]; t[2] = v[3]; t[3] = v[1]; t[4] = v[2]; t[5] = v[3];
+        }
+        if (alt) alt[q] = (uint8_t)use13;
+        if (m02) m02[q] = a;
+        if (m13) m13[q] = b;
+    }
     return 0;
 }

@@ -24,6 +24,7 @@ struct sn_mesh {
     int64_t np, nq, ns;
     sn::MeshArrays a;
     float *smooth_scratch;
+    int32_t *tris;
     cudaMemPool_t pool;
 };
 
@@ -439,7 +440,15 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
 
 sn_status sn_smooth(sn_mesh *m, int iterations, float relaxation, float constraint_distance)
 {
+    return sn_smooth_ex(m, iterations, relaxation, constraint_distance, SN_CONSTRAINT_BOX);
+}
+
+sn_status sn_smooth_ex(sn_mesh *m, int iterations, float relaxation, float constraint_distance,
+                       sn_constraint constraint)
+{
     g_last_error.clear();
+    if (constraint != SN_CONSTRAINT_BOX && constraint != SN_CONSTRAINT_SPHERE)
+        return fail(SN_EINVAL, "unknown constraint");
     if (!m) return fail(SN_EINVAL, "mesh is NULL");
     if (iterations < 0) return fail(SN_EINVAL, "iterations must be >= 0");
     if (!std::isfinite(relaxation) || relaxation < 0.f) return fail(SN_EINVAL, "relaxation must be finite and >= 0");
@@ -452,8 +461,30 @@ sn_status sn_smooth(sn_mesh *m, int iterations, float relaxation, float constrai
         if (r != SN_OK) return r;
     }
     cudaError_t e = sn::launch_smooth(m->a, m->np, iterations, relaxation, 0.5f * constraint_distance,
-                                      m->smooth_scratch, m->spacing, m->stream);
+                                      constraint == SN_CONSTRAINT_SPHERE, m->smooth_scratch, m->spacing, m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "smoothing launch");
+    return SN_OK;
+}
+
+sn_status sn_triangulate(sn_mesh *m, sn_tri_method method)
+{
+    g_last_error.clear();
+    if (!m) return fail(SN_EINVAL, "mesh is NULL");
+    if (method != SN_TRI_GREEDY && method != SN_TRI_SHORTEST && method != SN_TRI_MIN_AREA && method != SN_TRI_COPLANAR)
+        return fail(SN_EINVAL, "unknown triangulation method");
+    if (!m->tris) {
+        sn_status r = pool_alloc((void **)&m->tris, sizeof(int32_t) * 6 * (size_t)m->nq, m->pool, m->stream, "triangles");
+        if (r != SN_OK) return r;
+    }
+    cudaError_t e = sn::launch_triangulate(m->a, m->np, m->nq, (int)method, m->tris, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "triangulation launch");
+    return SN_OK;
+}
+
+sn_status sn_mesh_triangles(const sn_mesh *m, const int32_t **triangles)
+{
+    if (!m || !triangles) return fail(SN_EINVAL, "mesh or output is NULL");
+    *triangles = m->tris;
     return SN_OK;
 }
 
@@ -520,7 +551,8 @@ void sn_free(sn_mesh *m)
 {
     if (!m) return;
     void *ps[] = {m->a.points,    m->a.offsets, m->a.cells, m->a.quads, m->a.quad_labels, m->a.sten_off,
-                  m->a.sten_ids,  m->a.face_mask, m->a.meta,  m->a.nbr,   m->a.lut_x,       m->smooth_scratch};
+                  m->a.sten_ids,  m->a.face_mask, m->a.meta,  m->a.nbr,   m->a.lut_x,       m->smooth_scratch,
+                  m->tris};
     for (void *p : ps) pool_free(p, m->stream);
     std::free(m);
 }

@@ -109,7 +109,11 @@ cudaError_t launch_centre_lut(const MeshArrays &m, const int64_t dims[3], const 
 
 // launchers (sn_smooth.cu)
 cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float relaxation, float half,
-                          float *scratch, const double spacing[3], cudaStream_t st);
+                          int sphere, float *scratch, const double spacing[3], cudaStream_t st);
+
+// triangulation (sn_triangulate.cu): tris holds 6 * nq int32
+cudaError_t launch_triangulate(const MeshArrays &m, int64_t np, int64_t nq, int method, int32_t *tris,
+                               cudaStream_t st);
 cudaError_t launch_centres(const MeshArrays &m, int64_t np, cudaStream_t st);
 
 // detail message returned by sn_last_error() on this thread (sn_api.cu)

@@ -38,7 +38,18 @@ struct SweepArgs {
     float lam, h;
     float spx, spy, spz;
     int first, last; // first sweep: offsets are all zero; last sweep: also write world coordinates
+    int sphere;      // constrain |o| <= h instead of |o_a| <= h per axis
 };
+
+// The constraint of Sec. 2.2: a box of half-width h per axis, or a ball of radius h.
+__device__ __forceinline__ float3 constrain(float3 v, float h, int sphere)
+{
+    if (!sphere) return make_float3(fminf(fmaxf(v.x, -h), h), fminf(fmaxf(v.y, -h), h), fminf(fmaxf(v.z, -h), h));
+    const float r2 = v.x * v.x + v.y * v.y + v.z * v.z;
+    if (r2 <= h * h) return v;
+    const float s = h / sqrtf(r2);
+    return make_float3(v.x * s, v.y * s, v.z * s);
+}
 
 // world coordinate of a cell centre (hi, lo) displaced by spacing * o
 __device__ __forceinline__ float world(float2 c, float sp, float o) { return c.x + (c.y + sp * o); }
@@ -75,9 +86,8 @@ __device__ __forceinline__ void sweep_point(const SweepArgs &a, uint32_t i, floa
         if (dpz) add_diff(acc, ld3(oin, i + dpz), o);
     }
     const float ln = a.lam * kInv[n];
-    const float nx = fminf(fmaxf(o.x + ln * acc.x, -a.h), a.h);
-    const float ny = fminf(fmaxf(o.y + ln * acc.y, -a.h), a.h);
-    const float nz = fminf(fmaxf(o.z + ln * acc.z, -a.h), a.h);
+    const float3 nv = constrain(make_float3(o.x + ln * acc.x, o.y + ln * acc.y, o.z + ln * acc.z), a.h, a.sphere);
+    const float nx = nv.x, ny = nv.y, nz = nv.z;
     float *dst = a.oout + 3ull * i;
     dst[0] = nx;
     dst[1] = ny;
@@ -109,9 +119,8 @@ __device__ __forceinline__ void sweep_point_csr(const SweepArgs &a, uint32_t i)
         add_diff(acc, ld3(oin, (uint32_t)j), o);
     }
     const float ln = a.lam * kInv[n < 7 ? n : 0];
-    const float nx = fminf(fmaxf(o.x + ln * acc.x, -a.h), a.h);
-    const float ny = fminf(fmaxf(o.y + ln * acc.y, -a.h), a.h);
-    const float nz = fminf(fmaxf(o.z + ln * acc.z, -a.h), a.h);
+    const float3 nv = constrain(make_float3(o.x + ln * acc.x, o.y + ln * acc.y, o.z + ln * acc.z), a.h, a.sphere);
+    const float nx = nv.x, ny = nv.y, nz = nv.z;
     float *dst = a.oout + 3ull * i;
     dst[0] = nx;
     dst[1] = ny;
@@ -183,7 +192,7 @@ cudaError_t launch_centres(const MeshArrays &m, int64_t np, cudaStream_t st)
 // Runs `iterations` sweeps from zero offsets; the result ends in m.offsets and
 // the world positions in m.points.  `scratch` holds 3*np floats.
 cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float relaxation, float half,
-                          float *scratch, const double spacing[3], cudaStream_t st)
+                          int sphere, float *scratch, const double spacing[3], cudaStream_t st)
 {
     if (np == 0) return cudaSuccess;
     if (iterations == 0) return launch_centres(m, np, st);
@@ -201,6 +210,7 @@ cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float
     a.np = np;
     a.lam = relaxation;
     a.h = half;
+    a.sphere = sphere;
     a.spx = (float)spacing[0];
     a.spy = (float)spacing[1];
     a.spz = (float)spacing[2];

@@ -41,6 +41,9 @@ SIGNATURES = {
     "sn_extract": (ctypes.c_int, [_P, ctypes.c_int, _I64P, _DP, _DP, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int64,
                                   ctypes.c_uint32, _P, ctypes.POINTER(_P)]),
     "sn_smooth": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_float, ctypes.c_float]),
+    "sn_smooth_ex": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_int]),
+    "sn_triangulate": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sn_mesh_triangles": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
     "sn_mesh_counts": (ctypes.c_int, [_P, _I64P, _I64P, _I64P]),
     "sn_mesh_device_arrays": (ctypes.c_int, [_P] + [ctypes.POINTER(_P)] * 6),
     "sn_mesh_face_masks": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
@@ -177,8 +180,32 @@ def sn_extract(labels, spacing=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0), selected
     return Mesh(out.value, tcode, dims, spacing, origin)
 
 
+SN_CONSTRAINT_BOX, SN_CONSTRAINT_SPHERE = 0, 1
+SN_TRI = {"greedy": 0, "shortest": 1, "min_area": 2, "coplanar": 3}
+
+
 def sn_smooth(mesh: Mesh, iterations=16, relaxation=0.5, constraint_distance=1.0):
     _check(load().sn_smooth(mesh.handle, int(iterations), float(relaxation), float(constraint_distance)))
+
+
+def sn_smooth_ex(mesh: Mesh, iterations=16, relaxation=0.5, constraint_distance=1.0, sphere=False):
+    _check(load().sn_smooth_ex(mesh.handle, int(iterations), float(relaxation), float(constraint_distance),
+                               SN_CONSTRAINT_SPHERE if sphere else SN_CONSTRAINT_BOX))
+
+
+def sn_triangulate(mesh: Mesh, method="shortest"):
+    _check(load().sn_triangulate(mesh.handle, SN_TRI[method]))
+
+
+def sn_mesh_triangles(mesh: Mesh):
+    """The mesh's triangles as a borrowed torch tensor (2*n_quads, 3), or None before sn_triangulate."""
+    torch = _torch()
+    p = ctypes.c_void_p()
+    _check(load().sn_mesh_triangles(mesh.handle, ctypes.byref(p)))
+    if not p.value:
+        return None
+    _, q, _ = sn_mesh_counts(mesh)
+    return torch.as_tensor(_CudaArray(p.value, (2 * q, 3), "<i4"), device="cuda")
 
 
 def sn_mesh_counts(mesh: Mesh):

@@ -108,10 +108,12 @@ def one_ring(n_points, quads_ids):
     return nb
 
 
-def dense_jacobi_world(cells, quads_ids, spacing, origin, iterations, relaxation, constraint):
+def dense_jacobi_world(cells, quads_ids, spacing, origin, iterations, relaxation, constraint, sphere=False):
     """Eq. 1 in world units with a dense adjacency matrix built from the quad edges.
 
-    P <- clamp(P + lambda * (D^-1 A P - P)), box = cell centre +- (d/2)*spacing.
+    P <- clamp(P + lambda * (D^-1 A P - P)), box = cell centre +- (d/2)*spacing;
+    with sphere=True (isotropic spacing only) the displacement from the centre is
+    scaled back onto the ball of radius (d/2)*spacing when it leaves it.
     """
     cells = np.asarray(cells, dtype=np.float64)
     n = cells.shape[0]
@@ -129,7 +131,14 @@ def dense_jacobi_world(cells, quads_ids, spacing, origin, iterations, relaxation
     for _ in range(iterations):
         mean = (A @ P) / deg[:, None]
         P = P + relaxation * (mean - P)
-        P = np.minimum(np.maximum(P, centre - half), centre + half)
+        if sphere:
+            disp = P - centre
+            r = np.sqrt((disp ** 2).sum(axis=1))
+            R = half[0]
+            scale = np.where(r > R, R / np.where(r > 0, r, 1.0), 1.0)
+            P = centre + disp * scale[:, None]
+        else:
+            P = np.minimum(np.maximum(P, centre - half), centre + half)
     return P
 
 

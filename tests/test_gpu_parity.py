@@ -114,6 +114,27 @@ def test_zero_iterations_and_zero_relaxation():
     parity(lab, iterations=6, relaxation=1.0, constraint=0.0)
 
 
+def test_sphere_constraint():
+    lab = sn_synth.ellipsoids((60, 52, 44), 6, 5.0, 16.0, np.uint16, seed=12)
+    parity(lab, iterations=16, sphere=True)
+    parity(lab, spacing=(0.8, 0.8, 0.8), iterations=7, relaxation=0.9, constraint=0.6, sphere=True)
+
+
+TRI = ("greedy", "shortest", "min_area", "coplanar")
+
+
+def test_triangulation_unsmoothed_exact():
+    lab = sn_synth.ellipsoids((64, 64, 64), 6, 6.0, 20.0, np.uint16, seed=13)
+    parity(lab, spacing=(0.9, 1.1, 1.7), iterations=0, triangulate=TRI)
+
+
+def test_triangulation_smoothed():
+    w = sn_synth.config1()
+    parity(w.labels, iterations=16, triangulate=TRI)
+    lab = sn_synth.atlas((96, 80, 72), n_seeds=12, seed=14)
+    parity(lab, spacing=(1.0, 1.0, 2.0), iterations=9, sphere=True, triangulate=TRI)
+
+
 def test_determinism():
     from gpu_util import run_gpu
     lab = sn_synth.ellipsoids((64, 64, 64), 6, 6.0, 20.0, np.uint16, seed=10)
@@ -130,3 +151,13 @@ def test_config2_full_size():
     ref = parity(w.labels, w.spacing, w.origin, iterations=w.iterations, relaxation=w.relaxation,
                  constraint=w.constraint)
     assert ref.n_points > 1_000_000
+
+
+def test_config3_full_size():
+    # 1024x1024x512 uint32, 50,000 Voronoi cells with (1,1,4) spacing and 5% gaps:
+    # ~1.4e8 points, whose -z/+z neighbours are beyond the packed record's reach,
+    # so the sweeps take the CSR path at full size
+    w = sn_synth.config3()
+    ref = parity(w.labels, w.spacing, w.origin, iterations=w.iterations, relaxation=w.relaxation,
+                 constraint=w.constraint)
+    assert ref.n_points > 100_000_000

@@ -256,3 +256,81 @@ def test_flat_interface_motion_spreads_one_ring_per_iteration():
         assert np.all(off[:, 0] == 0.0)
         assert np.all(off[ring >= t] == 0.0)
         assert np.all(np.abs(off[ring == t - 1]).sum(axis=1) > 0.0)
+
+
+# ------------------------------------------------------------ sphere constraint
+def test_sphere_constraint_closed_form_unit_voxel():
+    # every point moves along its cube diagonal: its per-axis distance h from the
+    # cube centre obeys h' = max(h(1 - 2 lambda/3), 1/2 - d/(2 sqrt 3)) with the ball
+    lab = np.zeros((3, 3, 3), dtype=np.uint16)
+    lab[1, 1, 1] = 7
+    m = oracle.extract(lab)
+    for it, lam, d in [(16, 0.5, 1.0), (3, 0.5, 1.0), (6, 0.8, 0.4), (1, 0.5, 1.0)]:
+        h = 0.5
+        for _ in range(it):
+            h = max(h * (1.0 - 2.0 * lam / 3.0), 0.5 - d / (2.0 * np.sqrt(3.0)))
+        off, pts = oracle.smooth(m, iterations=it, relaxation=lam, constraint=d, sphere=True)
+        np.testing.assert_allclose(np.abs(pts - 1.0), h, rtol=0, atol=1e-14)
+        assert np.all(np.sqrt((off ** 2).sum(axis=1)) <= 0.5 * d + 1e-15)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_sphere_smoothing_matches_dense_jacobi(seed):
+    lab, m = _small_mesh(seed)
+    for it, lam, d in [(16, 0.5, 1.0), (7, 0.9, 0.6)]:
+        _, pts = oracle.smooth(m, (1.5, 1.5, 1.5), (2.0, -1.0, 0.5), it, lam, d, sphere=True)
+        ref = brute.dense_jacobi_world(m.cells, m.quads, (1.5, 1.5, 1.5), (2.0, -1.0, 0.5), it, lam, d, sphere=True)
+        np.testing.assert_allclose(pts, ref, rtol=0, atol=1e-11)
+
+
+# ---------------------------------------------------------------- triangulation
+def _quad_points(lift):
+    # unit square in z = 0 with vertex `lift` raised to z = 1 (a folded quad)
+    p = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0]], dtype=np.float32)
+    p[lift, 2] = 1.0
+    return p, np.array([[0, 1, 2, 3]], dtype=np.int32)
+
+
+def test_triangulation_choices_on_folded_quads():
+    # lifting v2 (or v0) lengthens diagonal v0-v2 (sqrt 3 vs sqrt 2); the split
+    # along v1-v3 then has twice-area 1 + sqrt(3) = 2.732 < 2 sqrt(2) = 2.828 for
+    # v0-v2, and normals at cosine 1/sqrt(3) = 0.577 > 1/2: every criterion picks
+    # v1-v3.  Lifting v1 or v3 mirrors the quad and every criterion picks v0-v2.
+    for lift, want_alt in [(2, True), (3, False), (0, True), (1, False)]:
+        pts, quads = _quad_points(lift)
+        for method in ("shortest", "min_area", "coplanar"):
+            tris, alt, metric = oracle.triangulate(pts, quads, method)
+            assert bool(alt[0]) == want_alt, (lift, method)
+        tris, alt, _ = oracle.triangulate(pts, quads, "greedy")
+        assert not alt[0] and tris.tolist() == [[0, 1, 2], [0, 2, 3]]
+    pts, quads = _quad_points(2)
+    _, _, metric = oracle.triangulate(pts, quads, "min_area")
+    np.testing.assert_allclose(metric[0], [2.0 * np.sqrt(2.0), 1.0 + np.sqrt(3.0)], rtol=1e-6)
+    _, _, metric = oracle.triangulate(pts, quads, "coplanar")
+    np.testing.assert_allclose(metric[0], [0.5, 1 / np.sqrt(3.0)], rtol=1e-6)
+    tris, _, _ = oracle.triangulate(pts, quads, "shortest")
+    assert tris.tolist() == [[0, 1, 3], [1, 2, 3]]
+
+
+@pytest.mark.parametrize("method", ["greedy", "shortest", "min_area", "coplanar"])
+def test_triangulation_invariants(method):
+    lab, m = _small_mesh(11, (7, 8, 9), 4)
+    _, pts = oracle.smooth(m, iterations=8, relaxation=0.5, constraint=1.0)
+    tris, alt, _ = oracle.triangulate(pts.astype(np.float32), m.quads, method)
+    assert tris.shape == (2 * m.n_quads, 3)
+    for q in range(m.n_quads):
+        v = [int(x) for x in m.quads[q]]
+        t0, t1 = [int(x) for x in tris[2 * q]], [int(x) for x in tris[2 * q + 1]]
+        assert set(t0) | set(t1) == set(v)
+        diag = set(t0) & set(t1)
+        assert diag == ({v[1], v[3]} if alt[q] else {v[0], v[2]})
+        # each triangle keeps the quad's cyclic order (hence its winding)
+        for t in (t0, t1):
+            k = [v.index(x) for x in t]
+            assert k in ([0, 1, 2], [0, 2, 3], [0, 1, 3], [1, 2, 3])
+    # on the unsmoothed mesh every triangle normal points along the quad's axis
+    c = oracle.triangulate(m.points.astype(np.float32), m.quads, method)[0]
+    p = m.points[c]
+    n = np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0])
+    axis_of = np.argmax(np.abs(n), axis=1)
+    assert np.all(n[np.arange(len(n)), axis_of] > 0)
