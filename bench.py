@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-slab", type=int, default=0, help="z-slices of the map the oracle baseline runs on")
+    p.add_argument("--label-sweep", action="store_true",
+                   help="time extract + smooth with the first k of 128 sphere labels selected, k = 1..128")
     return p.parse_args()
 
 
@@ -150,9 +152,9 @@ def kernel_units(name, V, b, P, Q, S, n):
     """(algorithmic bytes per launch, unit description) for each kernel."""
     if name == "k_smooth":
         return 24 * P, "24 B per point (read+write one float3 offset)"
-    if name == "k_planes":
+    if name in ("k_count", "k_planes"):
         return V * b, "%d B per voxel (labels read once)" % b
-    if name == "k_emit":
+    if name in ("k_emit_tile", "k_emit"):
         return 12 * P + (16 + 2 * b) * Q + 8 * (P + 1) + 4 * S, "mesh bytes written once"
     return None, None
 
@@ -408,10 +410,55 @@ def run_ours(args):
     return 0
 
 
+def run_label_sweep(args):
+    """Slowdown as the number of extracted labels grows: the 512^3 uint16 map of 128 overlapping
+    spheres (the paper's Synthetic dataset shape), labels 1..k selected, the rest background."""
+    import torch
+
+    from paper_2401_14906_gb300 import build, sn
+    build.build()
+    sn.load()
+    w = make_workload("synthetic")
+    lab = to_device(w.labels)
+    stream = torch.cuda.Stream()
+    rows = []
+    with torch.cuda.stream(stream):
+        for k in (1, 2, 4, 8, 16, 32, 64, 128):
+            sel = list(range(1, k + 1))
+
+            def step():
+                m = sn.sn_extract(lab, w.spacing, w.origin, selected=sel, background=0, stream=stream)
+                sn.sn_smooth(m, w.iterations, w.relaxation, w.constraint)
+                cnt = m.counts
+                m.free()
+                return cnt
+
+            for _ in range(max(2, args.warmup)):
+                cnt = step()
+            torch.cuda.synchronize()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(args.steps):
+                step()
+            z.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(z) / args.steps
+            rows.append({"labels": k, "ms_per_step": ms, "points": cnt[0], "quads": cnt[1]})
+    base = rows[0]["ms_per_step"]
+    for r in rows:
+        r["slowdown"] = r["ms_per_step"] / base
+    print(json.dumps({"metric": "extract+smooth time vs number of selected labels", "unit": "ms",
+                      "config": workload_config(w, {"sweep": "selected = labels 1..k"}), "steps": args.steps,
+                      "results": rows}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.label_sweep:
+        return run_label_sweep(args)
     return run_ours(args)
 
 

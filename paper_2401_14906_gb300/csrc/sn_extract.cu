@@ -349,8 +349,20 @@ __global__ void __launch_bounds__(256, 4) k_count(const T *__restrict__ lab, Cla
             }
         }
         for (int e = tid; e < 3 * TY + 2; e += nthr) cnt[e] = 0;
-        const T *S0 = reinterpret_cast<const T *>(slots + (size_t)((kk - k0) % kCountSlots) * tl.slot_bytes);
-        const T *S1 = reinterpret_cast<const T *>(slots + (size_t)((kk + 1 - k0) % kCountSlots) * tl.slot_bytes);
+        T *S0w = reinterpret_cast<T *>(slots + (size_t)((kk - k0) % kCountSlots) * tl.slot_bytes);
+        T *S1w = reinterpret_cast<T *>(slots + (size_t)((kk + 1 - k0) % kCountSlots) * tl.slot_bytes);
+        const T *S0 = S0w, *S1 = S1w;
+        if (MODE != CLASS_ALL && FAST) {
+            // replace each newly arrived label by its class (Sec. 3.1), so that the
+            // packed compares below compare classes; slice kk arrived as slice kk+1
+            // of the previous step unless this is the first step
+            __syncthreads();
+            const int64_t n = (int64_t)rows_ld * nx;
+            if (kk == k0 && have)
+                for (int64_t e = tid; e < n; e += nthr) S0w[e] = (T)kappa<MODE>(c, (uint32_t)S0w[e]);
+            if (have_next)
+                for (int64_t e = tid; e < n; e += nthr) S1w[e] = (T)kappa<MODE>(c, (uint32_t)S1w[e]);
+        }
         __syncthreads();
         // ---- Passes 1-2 for slice kk: one thread per (row, word)
         for (int it = tid; it < (TY + 1) * W; it += nthr) {
@@ -359,7 +371,9 @@ __global__ void __launch_bounds__(256, 4) k_count(const T *__restrict__ lab, Cla
             if (have && r < rows_ld) {
                 const T *row = S0 + (int64_t)r * nx;
                 const bool doY = r < rows_own && r + 1 < rows_ld;
-                edge_words<T, MODE, FAST>(c, row, row + nx, S1 + (int64_t)r * nx, nx, w, doY, have_next, xw, yw, zw);
+                // (the fast form compares classes already in shared memory)
+                edge_words<T, FAST ? (int)CLASS_ALL : MODE, FAST>(c, row, row + nx, S1 + (int64_t)r * nx, nx, w, doY,
+                                                                  have_next, xw, yw, zw);
                 if (r < rows_own && (xw | yw | zw)) atomicAdd(&cnt[r], __popc(xw) + __popc(yw) + __popc(zw));
             }
             PL(cur, 0, r)[w] = xw;
@@ -864,10 +878,8 @@ template <typename T, int MODE>
 cudaError_t count_t(const void *labels, const Classifier &c, const Geometry &g, const ExtractScratch &s,
                     const CountTiling &tl, size_t smem, DevTotals *tot, cudaStream_t st)
 {
-    // packed compares need every value to be its own class and 16-byte aligned rows
-    if constexpr (MODE == CLASS_ALL) {
-        if (tl.aligned) return count_f<T, MODE, true>(labels, c, g, s, tl, smem, tot, st);
-    }
+    // packed compares need rows on 16-byte boundaries (labels are classified in shared memory first)
+    if (tl.aligned) return count_f<T, MODE, true>(labels, c, g, s, tl, smem, tot, st);
     return count_f<T, MODE, false>(labels, c, g, s, tl, smem, tot, st);
 }
 
