@@ -313,6 +313,7 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
     g.WS = (g.W + 3) / 4 * 4;
     g.Rs = ny * nz;
     g.Rc = (ny + 1) * (nz + 1);
+    g.lp = nx;
     const int ntiles = (int)((g.Rc + sn::kScanTile - 1) / sn::kScanTile);
 
     sn::ExtractScratch s;

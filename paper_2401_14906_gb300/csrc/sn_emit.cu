@@ -15,7 +15,7 @@
 // popcount prefixes (one thread per row), lists its points and quads in
 // canonical order (list index = id minus the tile's first id) and gives each
 // to one thread.
-#include "sn_device.cuh"
+#include "sn_emit_tile.cuh"
 
 namespace sn {
 
@@ -23,336 +23,11 @@ namespace {
 
 using namespace dev;
 
-constexpr int kTileRows = 16;  // cell rows per tile, at most
-constexpr int kTileMaxW = 64;  // rows of up to 2047 cells; wider rows use the per-row kernel
-constexpr int kListCap = 2048; // list entries per pass
-
-struct TileGeom {
-    int ty;        // cell rows per tile
-    int W, WS;     // words per row, row stride in words
-    int ns;        // staged point-plane rows: 3 * (ty + 2)
-    uint64_t wdiv; // ceil(2^32 / W): it / W == (it * wdiv) >> 32
-};
-
-// shared-memory carve-up, in 4-byte words; every array starts on 16 bytes
-struct TileSmem {
-    int bar, P, planes, pre, base, F, dpre, qpre, soff, qoff, list, total;
-    __host__ __device__ static int up4(int v) { return (v + 3) & ~3; }
-    __host__ __device__ TileSmem(int ty, int W, int WS)
-    {
-        const int ns = 3 * (ty + 2);
-        bar = 0;                               // one mbarrier, padded to 16 bytes
-        P = 4;                                 // [ns][WS] point-plane words
-        planes = P + ns * WS;                  // [2 dk][3 plane][ty+1 rows][WS] X/Y/Z words
-        pre = planes + 2 * 3 * (ty + 1) * WS;  // [ns][W] points before the word, within the row
-        base = pre + up4(ns * W);              // [ns] first point id of the row
-        F = base + up4(ns);                    // [ty][6][W] face planes of own rows
-        dpre = F + up4(ty * 6 * W);            // [ty][W] stencil entries before the word
-        qpre = dpre + up4(ty * W);             // [ty][W] quads before the word
-        soff = qpre + up4(ty * W);             // [ty] int64 first stencil entry of the row
-        qoff = soff + 2 * ty;                  // [ty] int64 first quad of the sample row
-        list = qoff + 2 * ty;                  // [kListCap]
-        total = list + kListCap;
-    }
-};
-
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_emit_tile(const T *__restrict__ lab, Classifier c, Geometry g,
                                                    ExtractScratch s, MeshArrays m, DevTotals *tot, TileGeom tg)
 {
-    extern __shared__ __align__(128) uint32_t sm[];
-    const int TY = tg.ty, W = tg.W, WS = tg.WS, NS = tg.ns;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x, nwarps = nthr >> 5;
-    const int64_t ny = g.ny, nz = g.nz, nx = g.nx, ny1 = ny + 1, nz1 = nz + 1;
-    const int64_t c0 = (int64_t)blockIdx.x * TY; // first cy + 1 of the tile
-    const int64_t czc = blockIdx.y;              // cz + 1
-    const int64_t cz = czc - 1;
-    const int n = (int)(ny1 - c0 < TY ? ny1 - c0 : TY);
-    const TileSmem L(TY, W, WS);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.bar);
-    uint32_t *sP = sm + L.P;
-    uint32_t *sPl = sm + L.planes;
-    int32_t *sPre = reinterpret_cast<int32_t *>(sm + L.pre);
-    int32_t *sBase = reinterpret_cast<int32_t *>(sm + L.base);
-    uint32_t *sF = sm + L.F;
-    int32_t *sDpre = reinterpret_cast<int32_t *>(sm + L.dpre);
-    int32_t *sQpre = reinterpret_cast<int32_t *>(sm + L.qpre);
-    int64_t *sSoff = reinterpret_cast<int64_t *>(sm + L.soff);
-    int64_t *sQoff = reinterpret_cast<int64_t *>(sm + L.qoff);
-    uint32_t *sList = sm + L.list;
-    const int64_t NP = tot->n_points, NQ = tot->n_quads, NS_ = tot->n_stencil;
-
-    // own cell row lr in [0, n): cy = c0 - 1 + lr; its sample row (cy, cz) exists iff cy >= 0 && cz >= 0
-    const int64_t rc0 = c0 + ny1 * czc; // cell row index of lr = 0
-    bool work = false;
-    for (int lr = tid; lr < n; lr += nthr) {
-        const int64_t cy = c0 - 1 + lr;
-        work |= s.cntP[rc0 + lr] != 0;
-        if (cy >= 0 && cz >= 0) work |= s.cntQ[cy + ny * cz] != 0;
-    }
-    if (!__syncthreads_or(work)) return; // trimmed tile
-
-    // ---- staging: runs of rows copied by TMA; rows outside the volume are zeroed.
-    // point-plane slot (dz, lr) = dz * (TY + 2) + lr + 1, dz 0/1/2 = slices cz-1/cz/cz+1, lr in [-1, TY]
-    // plane row (dk, p, lr) = (dk * 3 + p) * (TY + 1) + lr: sample row j = c0 - 1 + lr of slice cz + dk
-    int pr_lo[3], pr_hi[3]; // point-plane rows [lo, hi) copied for each dz, in lr
-    for (int dz = 0; dz < 3; ++dz) {
-        const int64_t czz = czc - 1 + dz;
-        int lo = dz == 2 ? 0 : -1, hi = dz == 1 ? n + 1 : n;
-        if (c0 + lo < 0) lo = (int)-c0;
-        if (c0 + hi > ny1) hi = (int)(ny1 - c0);
-        if (czz < 0 || czz >= nz1 || hi < lo) hi = lo;
-        pr_lo[dz] = lo;
-        pr_hi[dz] = hi;
-    }
-    int pl_lo[2], pl_hi[2]; // X/Y/Z rows [lo, hi) copied for each dk, in lr
-    for (int dk = 0; dk < 2; ++dk) {
-        const int64_t k = cz + dk;
-        int lo = c0 == 0 ? 1 : 0, hi = n + 1;
-        if (c0 - 1 + hi > ny) hi = (int)(ny - (c0 - 1));
-        if (k < 0 || k >= nz || hi < lo) hi = lo;
-        pl_lo[dk] = lo;
-        pl_hi[dk] = hi;
-    }
-    for (int it = tid; it < NS * WS; it += nthr) {
-        const int slot = it / WS, dz = slot / (TY + 2), lr = slot - dz * (TY + 2) - 1;
-        if (lr < pr_lo[dz] || lr >= pr_hi[dz]) sP[it] = 0u;
-    }
-    for (int it = tid; it < 6 * (TY + 1) * WS; it += nthr) {
-        const int r = it / WS, dk = r / (3 * (TY + 1)), lr = r % (TY + 1);
-        if (lr < pl_lo[dk] || lr >= pl_hi[dk]) sPl[it] = 0u;
-    }
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        uint32_t bytes = 0;
-        for (int dz = 0; dz < 3; ++dz) bytes += (uint32_t)((pr_hi[dz] - pr_lo[dz]) * WS * 4);
-        for (int dk = 0; dk < 2; ++dk) bytes += 3u * (uint32_t)((pl_hi[dk] - pl_lo[dk]) * WS * 4);
-        mbar_expect_tx(bar, bytes);
-        for (int dz = 0; dz < 3; ++dz) {
-            if (pr_hi[dz] <= pr_lo[dz]) continue;
-            const int64_t row = c0 + pr_lo[dz] + ny1 * (czc - 1 + dz);
-            bulk_load(sP + (dz * (TY + 2) + pr_lo[dz] + 1) * WS, s.P + row * WS,
-                      (uint32_t)((pr_hi[dz] - pr_lo[dz]) * WS * 4), bar);
-        }
-        for (int dk = 0; dk < 2; ++dk) {
-            if (pl_hi[dk] <= pl_lo[dk]) continue;
-            const int64_t row = (c0 - 1 + pl_lo[dk]) + ny * (cz + dk);
-            const uint32_t nb = (uint32_t)((pl_hi[dk] - pl_lo[dk]) * WS * 4);
-            bulk_load(sPl + ((dk * 3 + 0) * (TY + 1) + pl_lo[dk]) * WS, s.X + row * WS, nb, bar);
-            bulk_load(sPl + ((dk * 3 + 1) * (TY + 1) + pl_lo[dk]) * WS, s.Y + row * WS, nb, bar);
-            bulk_load(sPl + ((dk * 3 + 2) * (TY + 1) + pl_lo[dk]) * WS, s.Z + row * WS, nb, bar);
-        }
-    }
-    for (int slot = tid; slot < NS; slot += nthr) {
-        const int dz = slot / (TY + 2), lr = slot - dz * (TY + 2) - 1;
-        sBase[slot] = (lr >= pr_lo[dz] && lr < pr_hi[dz]) ? (int32_t)s.offP[c0 + lr + ny1 * (czc - 1 + dz)] : 0;
-    }
-    for (int lr = tid; lr < n; lr += nthr) {
-        const int64_t cy = c0 - 1 + lr;
-        sSoff[lr] = s.offS[rc0 + lr];
-        sQoff[lr] = (cy >= 0 && cz >= 0) ? s.offQ[cy + ny * cz] : 0;
-    }
-    if (tid == 0 && !mbar_wait(bar, 0)) atomicOr(&tot->error, 4);
-    __syncthreads();
-
-    auto PL = [&](int dk, int p, int lr) -> const uint32_t * { return sPl + ((dk * 3 + p) * (TY + 1) + lr) * WS; };
-    auto slot_of = [&](int dz, int lr) { return dz * (TY + 2) + lr + 1; };
-
-    // ---- face planes of own cell rows, one thread per word
-    for (int it = tid; it < n * W; it += nthr) {
-        const int lr = (int)(((uint64_t)(uint32_t)it * tg.wdiv) >> 32), w = it - lr * W;
-        // sample rows a = (lr, dk0), b = (lr+1, dk0), c = (lr, dk1), d = (lr+1, dk1)
-        const uint32_t *aX = PL(0, 0, lr), *bX = PL(0, 0, lr + 1), *cX = PL(1, 0, lr), *dX = PL(1, 0, lr + 1);
-        const uint32_t *aY = PL(0, 1, lr), *cY = PL(1, 1, lr), *aZ = PL(0, 2, lr), *bZ = PL(0, 2, lr + 1);
-        const uint32_t Xa = aX[w], Xb = bX[w], Xc = cX[w], Xd = dX[w], Ya = aY[w], Yc = cY[w], Za = aZ[w], Zb = bZ[w];
-        uint32_t pXa = 0, pXb = 0, pXc = 0, pXd = 0, pYa = 0, pYc = 0, pZa = 0, pZb = 0;
-        if (w > 0) {
-            pXa = aX[w - 1];
-            pXb = bX[w - 1];
-            pXc = cX[w - 1];
-            pXd = dX[w - 1];
-            pYa = aY[w - 1];
-            pYc = cY[w - 1];
-            pZa = aZ[w - 1];
-            pZb = bZ[w - 1];
-        }
-        uint32_t F[6];
-        F[0] = shl1(Ya | Yc | Za | Zb, pYa | pYc | pZa | pZb);
-        F[1] = Ya | Yc | Za | Zb;
-        F[2] = shl1(Xa | Xc | Za, pXa | pXc | pZa) | Za;
-        F[3] = shl1(Xb | Xd | Zb, pXb | pXd | pZb) | Zb;
-        F[4] = shl1(Xa | Xb | Ya, pXa | pXb | pYa) | Ya;
-        F[5] = shl1(Xc | Xd | Yc, pXc | pXd | pYc) | Yc;
-        int deg = 0;
-#pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            sF[(lr * 6 + f) * W + w] = F[f];
-            deg += __popc(F[f]);
-        }
-        sDpre[lr * W + w] = deg;
-        sQpre[lr * W + w] = __popc(Xa) + __popc(Ya) + __popc(Za);
-    }
-    __syncthreads();
-    // ---- per-row exclusive prefixes, one thread per row
-    for (int r = tid; r < NS + 2 * n; r += nthr) {
-        int run = 0;
-        if (r < NS) {
-            for (int w = 0; w < W; ++w) {
-                sPre[r * W + w] = run;
-                run += __popc(sP[r * WS + w]);
-            }
-        } else {
-            int32_t *a = r < NS + n ? sDpre + (r - NS) * W : sQpre + (r - NS - n) * W;
-            for (int w = 0; w < W; ++w) {
-                const int v = a[w];
-                a[w] = run;
-                run += v;
-            }
-        }
-    }
-    __syncthreads();
-
-    // rank of cell bit p in staged row `slot`
-    auto rank = [&](int slot, int64_t p) -> int32_t {
-        const int w = (int)(p >> 5);
-        return sBase[slot] + sPre[slot * W + w] + __popc(sP[slot * WS + w] & ((1u << (p & 31)) - 1u));
-    };
-
-    // ---- points and stencils, in id order
-    const int last = slot_of(1, n - 1);
-    const int32_t pbase = sBase[slot_of(1, 0)];
-    const int32_t pend = sBase[last] + sPre[last * W + (W - 1)] + __popc(sP[last * WS + (W - 1)]);
-    int32_t reach = 1;
-    for (int32_t win = pbase; win < pend; win += kListCap) {
-        __syncthreads();
-        for (int lr = warp; lr < n; lr += nwarps) {
-            const int so = slot_of(1, lr);
-            for (int w = lane; w < W; w += 32) {
-                uint32_t bits = sP[so * WS + w];
-                int32_t idx = sBase[so] + sPre[so * W + w];
-                while (bits) {
-                    const int b = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    if (idx >= win && idx < win + kListCap)
-                        sList[idx - win] = ((uint32_t)lr << 24) | ((uint32_t)w << 5) | (uint32_t)b;
-                    ++idx;
-                }
-            }
-        }
-        __syncthreads();
-        const int cnt = (pend - win) < kListCap ? (pend - win) : kListCap;
-        for (int k = tid; k < cnt; k += nthr) {
-            const uint32_t e = sList[k];
-            const int lr = (int)(e >> 24), w = (int)((e >> 5) & 0x7ffffu), b = (int)(e & 31u);
-            const int32_t id = win + k;
-            if (id < 0 || id >= NP) continue;
-            const uint32_t lt = (1u << b) - 1u;
-            const int64_t p = (int64_t)w * 32 + b;
-            const int64_t cx = p - 1, cy = c0 - 1 + lr;
-            float *pt = m.points + 3 * (int64_t)id;
-            pt[0] = m.lut_x[cx + 1].x;
-            pt[1] = m.lut_y[cy + 1].x;
-            pt[2] = m.lut_z[cz + 1].x;
-            float *of = m.offsets + 3 * (int64_t)id;
-            of[0] = 0.f;
-            of[1] = 0.f;
-            of[2] = 0.f;
-            m.cells[id] = (uint64_t)(cx + 1) | ((uint64_t)(cy + 1) << 21) | ((uint64_t)(cz + 1) << 42);
-            uint32_t mask = 0;
-            int64_t so = sSoff[lr] + sDpre[lr * W + w];
-#pragma unroll
-            for (int f = 0; f < 6; ++f) {
-                const uint32_t fw = sF[(lr * 6 + f) * W + w];
-                so += __popc(fw & lt);
-                mask |= ((fw >> b) & 1u) << f;
-            }
-            m.face_mask[id] = (uint8_t)mask;
-            m.sten_off[id] = so;
-            if (so < 0 || so + __popc(mask) > NS_) continue;
-            int32_t *dst = m.sten_ids + so;
-            if (mask & 1u) *dst++ = id - 1;
-            if (mask & 2u) *dst++ = id + 1;
-            uint32_t dist[4] = {0u, 0u, 0u, 0u};
-            const int nbs[4] = {slot_of(1, lr - 1), slot_of(1, lr + 1), slot_of(0, lr), slot_of(2, lr)};
-#pragma unroll
-            for (int f = 2; f < 6; ++f)
-                if ((mask >> f) & 1u) {
-                    const int32_t nb = rank(nbs[f - 2], p);
-                    *dst++ = nb;
-                    const int32_t d = nb > id ? nb - id : id - nb;
-                    reach = d > reach ? d : reach;
-                    dist[f - 2] = (uint32_t)d & 0x7fffu;
-                }
-            m.nbr[id] = make_uint2(dist[0] | ((mask & 1u) << 15) | (dist[1] << 16) | (((mask >> 1) & 1u) << 31),
-                                   dist[2] | (dist[3] << 16));
-        }
-    }
-    reach = (int32_t)__reduce_max_sync(kFull, (unsigned)reach);
-    if (lane == 0 && reach > 1) atomicMax(m.meta, reach);
-
-    // ---- quads of sample rows (cy, cz), cy = c0 - 1 + lr, in quad order
-    const int lr_first = (c0 == 0) ? 1 : 0; // cy = -1 has no sample row
-    if (cz < 0 || lr_first >= n) return;
-    const int64_t qbase = sQoff[lr_first];
-    const int64_t qend = sQoff[n - 1] + sQpre[(n - 1) * W + (W - 1)] + __popc(PL(0, 0, n - 1)[W - 1]) +
-                         __popc(PL(0, 1, n - 1)[W - 1]) + __popc(PL(0, 2, n - 1)[W - 1]);
-    for (int64_t win = qbase; win < qend; win += kListCap) {
-        __syncthreads();
-        for (int lr = lr_first + warp; lr < n; lr += nwarps) {
-            const uint32_t *px = PL(0, 0, lr), *py = PL(0, 1, lr), *pz = PL(0, 2, lr);
-            for (int w = lane; w < W; w += 32) {
-                const uint32_t pw[3] = {px[w], py[w], pz[w]};
-                const int64_t w0 = sQoff[lr] + sQpre[lr * W + w];
-                // quad of (bit b, axis ax): quads of earlier bits, then earlier axes at b
-#pragma unroll
-                for (int ax = 0; ax < 3; ++ax) {
-                    uint32_t bits = pw[ax];
-                    while (bits) {
-                        const int b = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const uint32_t lt = (1u << b) - 1u;
-                        int64_t idx = w0 + __popc(pw[0] & lt) + __popc(pw[1] & lt) + __popc(pw[2] & lt);
-                        if (ax > 0) idx += (pw[0] >> b) & 1u;
-                        if (ax > 1) idx += (pw[1] >> b) & 1u;
-                        if (idx >= win && idx < win + kListCap)
-                            sList[idx - win] =
-                                ((uint32_t)lr << 24) | ((uint32_t)ax << 22) | ((uint32_t)w << 5) | (uint32_t)b;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        const int cnt = (int)((qend - win) < kListCap ? (qend - win) : kListCap);
-        for (int k = tid; k < cnt; k += nthr) {
-            const uint32_t e = sList[k];
-            const int lr = (int)(e >> 24), ax = (int)((e >> 22) & 3u), w = (int)((e >> 5) & 0x1ffffu),
-                      b = (int)(e & 31u);
-            const int64_t q = win + k;
-            if (q < 0 || q >= NQ) continue;
-            const int64_t i = (int64_t)w * 32 + b;
-            const int64_t j = c0 - 1 + lr;
-            const T *row = lab + (j + ny * cz) * nx;
-            // cell rows: 00 = (cy, cz), m0 = (cy-1, cz), 0m = (cy, cz-1), mm = (cy-1, cz-1)
-            const int s00 = slot_of(1, lr), sm0 = slot_of(1, lr - 1), s0m = slot_of(0, lr), smm = slot_of(0, lr - 1);
-            int4 v;
-            int64_t d1;
-            if (ax == 0) {
-                v = make_int4(rank(smm, i + 1), rank(s0m, i + 1), rank(s00, i + 1), rank(sm0, i + 1));
-                d1 = 1;
-            } else if (ax == 1) {
-                v = make_int4(rank(s0m, i), rank(s00, i), rank(s00, i + 1), rank(s0m, i + 1));
-                d1 = nx;
-            } else {
-                v = make_int4(rank(sm0, i), rank(sm0, i + 1), rank(s00, i + 1), rank(s00, i));
-                d1 = nx * ny;
-            }
-            reinterpret_cast<int4 *>(m.quads)[q] = v;
-            T *ql = reinterpret_cast<T *>(m.quad_labels) + 2 * q;
-            ql[0] = (T)kappa<MODE>(c, ldlab(row, i));
-            ql[1] = (T)kappa<MODE>(c, ldlab(row, i + d1));
-        }
-    }
+    emit_tile<T, MODE>(lab, c, g, s, m, tot, tg, blockIdx.x, blockIdx.y);
 }
 
 template <typename T, int MODE>

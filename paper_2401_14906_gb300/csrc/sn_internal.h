@@ -39,6 +39,7 @@ struct Geometry {
     int64_t WS; // row stride in words (W rounded up to a multiple of 4)
     int64_t Rs; // sample rows ny*nz
     int64_t Rc; // cell rows (ny+1)*(nz+1)
+    int64_t lp; // label row pitch in elements (nx for a caller's map; padded in the batched mode)
 };
 
 // Device temporaries of one extraction.
@@ -80,6 +81,23 @@ struct MeshArrays {
 };
 
 constexpr int32_t kPackedReach = 1 << 15; // packed records hold id distances below this
+
+// Tiling of the streaming counting pass (k_count): TY sample rows x KZ slices per CTA.
+struct CountTiling {
+    int ty, kz;
+    int W;
+    uint64_t wdiv;    // ceil(2^32 / W): it / W == (it * wdiv) >> 32 while it * W < 2^32
+    int slot_bytes;   // bytes of one label slot, rounded up to 128
+    int aligned;      // rows start on 16-byte boundaries: bulk copies allowed
+};
+
+// Tiling of the tiled emission (k_emit_tile): TY cell rows of one slice per CTA.
+struct TileGeom {
+    int ty;        // cell rows per tile
+    int W, WS;     // words per row, row stride in words
+    int ns;        // staged point-plane rows: 3 * (ty + 2)
+    uint64_t wdiv; // ceil(2^32 / W): it / W == (it * wdiv) >> 32
+};
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;

@@ -1,0 +1,139 @@
+// sn_scan.cuh -- the row prefix sum of Pass 3 (Sec. 2.3, 3.5): decoupled look-back
+// over tiles of cell rows; used by the single-map scan (sn_extract.cu) and by the
+// batched kernel (sn_batch.cu).
+#pragma once
+
+#include "sn_device.cuh"
+
+namespace sn {
+namespace dev {
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Exclusive scan of the three count arrays over rc in [0, Rc) in one pass:
+// each tile publishes its aggregate, then looks back over its predecessors
+// (32 at a time) until it meets an inclusive prefix.  The caller numbers tiles
+// in the order they start, so every awaited tile is already running.  Waits
+// are bounded; on timeout the error bit is set and the tile finishes.  The
+// counts are read through L2 (they may have been written by other CTAs of the
+// same launch).  The last tile also stores the totals.
+__device__ __forceinline__ void scan_tile(const Geometry &g, const ExtractScratch &s, DevTotals *tot, int tile,
+                                          int ntiles)
+{
+    __shared__ int64_t warp_tot[kScanThreads / 32][3];
+    __shared__ int64_t tile_excl[3];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t base = (int64_t)tile * kScanTile + (int64_t)tid * kScanItems;
+    const int32_t *cnt[3] = {s.cntP, s.cntS, s.cntQ};
+    int64_t *off[3] = {s.offP, s.offS, s.offQ};
+    int64_t v[3][kScanItems];
+    int64_t tsum[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int t = 0; t < kScanItems; ++t) {
+            const int64_t idx = base + t;
+            v[a][t] = idx < g.Rc ? (int64_t)__ldcg(cnt[a] + idx) : 0;
+            tsum[a] += v[a][t];
+        }
+    int64_t wincl[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        wincl[a] = warp_incl_scan64(tsum[a], lane);
+        if (lane == 31) warp_tot[warp][a] = wincl[a];
+    }
+    __syncthreads();
+    int64_t wbase[3] = {0, 0, 0}, agg[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        for (int w = 0; w < kScanThreads / 32; ++w) {
+            if (w < warp) wbase[a] += warp_tot[w][a];
+            agg[a] += warp_tot[w][a];
+        }
+    int64_t *aggv = s.scan_vals;                 // [3][ntiles]
+    int64_t *incv = s.scan_vals + 3 * ntiles;    // [3][ntiles]
+    if (warp == 0) {
+        int64_t ex[3] = {0, 0, 0};
+        if (tile == 0) {
+            if (lane == 0) {
+                for (int a = 0; a < 3; ++a) incv[a * ntiles] = agg[a];
+                __threadfence();
+                st_release(&s.scan_flags[0], 2);
+            }
+        } else {
+            if (lane == 0) {
+                for (int a = 0; a < 3; ++a) aggv[a * ntiles + tile] = agg[a];
+                __threadfence();
+                st_release(&s.scan_flags[tile], 1);
+            }
+            int pred = tile - 1;
+            bool done = false, timed_out = false;
+            while (!done) {
+                const int idx = pred - lane;
+                int f = 0;
+                if (idx >= 0) {
+                    int spins = 0;
+                    f = ld_acquire(&s.scan_flags[idx]);
+                    while (f == 0 && spins < kSpinLimit) {
+                        __nanosleep(64);
+                        f = ld_acquire(&s.scan_flags[idx]);
+                        ++spins;
+                    }
+                }
+                const bool to = __any_sync(kFull, idx >= 0 && f == 0);
+                const unsigned incl = __ballot_sync(kFull, idx >= 0 && f == 2);
+                const int stop = incl ? (__ffs(incl) - 1) : 31;
+                int64_t c[3] = {0, 0, 0};
+                if (idx >= 0 && lane <= stop && f != 0) {
+                    const int64_t *src = (f == 2) ? incv : aggv;
+                    for (int a = 0; a < 3; ++a) c[a] = __ldcg(src + a * ntiles + idx);
+                }
+                for (int a = 0; a < 3; ++a) ex[a] += warp_sum64(c[a]);
+                if (to) timed_out = true;
+                done = incl != 0 || to || pred - 31 <= 0;
+                pred -= 32;
+            }
+            if (lane == 0) {
+                if (timed_out) atomicOr(&tot->error, 1);
+                for (int a = 0; a < 3; ++a) incv[a * ntiles + tile] = ex[a] + agg[a];
+                __threadfence();
+                st_release(&s.scan_flags[tile], 2);
+            }
+        }
+        if (lane == 0)
+            for (int a = 0; a < 3; ++a) tile_excl[a] = ex[a];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int64_t run = tile_excl[a] + wbase[a] + wincl[a] - tsum[a];
+#pragma unroll
+        for (int t = 0; t < kScanItems; ++t) {
+            const int64_t idx = base + t;
+            if (idx < g.Rc) off[a][idx] = run;
+            run += v[a][t];
+        }
+    }
+    if (tile == ntiles - 1 && tid == 0) {
+        const int64_t tp = tile_excl[0] + agg[0], ts = tile_excl[1] + agg[1], tq = tile_excl[2] + agg[2];
+        s.offP[g.Rc] = tp;
+        s.offS[g.Rc] = ts;
+        s.offQ[g.Rc] = tq;
+        tot->n_points = tp;
+        tot->n_stencil = ts;
+        tot->n_quads = tq;
+    }
+}
+
+} // namespace dev
+} // namespace sn
