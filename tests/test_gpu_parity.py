@@ -45,6 +45,13 @@ def test_random_maps(dtype, seed):
     parity(lab, spacing=(0.7, 1.3, 2.0), origin=(-5.0, 3.0, 100.0), iterations=7, relaxation=0.6, constraint=0.8)
 
 
+@pytest.mark.parametrize("nx", [16, 48, 64, 128])
+def test_uint8_rows_on_16_byte_boundaries(nx):
+    """uint8 maps whose rows are 16-byte aligned take the per-sample counting form."""
+    lab = sn_synth.ellipsoids((nx, 37, 29), 5, 3.0, 11.0, np.uint8, seed=nx)
+    parity(lab, iterations=6)
+
+
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16, np.uint32])
 def test_ellipsoids_each_dtype(dtype):
     lab = sn_synth.ellipsoids((70, 45, 38), 6, 4.0, 15.0, dtype, seed=9)
