@@ -159,19 +159,30 @@ def kernel_units(name, V, b, P, Q, S, n):
     return None, None
 
 
+KERNEL_SOURCES = {
+    "k_smooth": ["paper_2401_14906_gb300/csrc/sn_smooth.cu", "paper_2401_14906_gb300/csrc/sn_sweep.cuh"],
+    "k_count": ["paper_2401_14906_gb300/csrc/sn_extract.cu", "paper_2401_14906_gb300/csrc/sn_count.cuh"],
+    "k_emit_tile": ["paper_2401_14906_gb300/csrc/sn_emit.cu", "paper_2401_14906_gb300/csrc/sn_emit_tile.cuh"],
+    "k_scan": ["paper_2401_14906_gb300/csrc/sn_extract.cu", "paper_2401_14906_gb300/csrc/sn_scan.cuh"],
+}
+
+
+def sources_sha(kernel):
+    """sha256 (16 hex digits) of the sources a kernel is built from, concatenated."""
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES.get(kernel, []):
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_for(kernel):
-    """Per-launch DRAM bytes from the committed ncu summary, if it matches the current source."""
+    """Per-launch DRAM bytes from the committed ncu summary, if it matches the current sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
-        d = json.load(open(path))
-        ent = d.get(kernel)
-        if not ent:
-            return None
-        src = os.path.join(ROOT, ent["source"])
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if sha != ent["source_sha256"]:
+        ent = json.load(open(path)).get(kernel)
+        if not ent or ent.get("sources_sha256") != sources_sha(kernel):
             return None
         return ent["dram_bytes_per_launch_full"]
     except Exception:
