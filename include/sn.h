@@ -191,6 +191,11 @@ sn_status sn_mesh_device_arrays(const sn_mesh *m, const float **points, const in
  * Sec. 3.3). */
 sn_status sn_mesh_face_masks(const sn_mesh *m, const uint8_t **face_masks);
 
+/* Borrowed device pointer to each point's generating cell, packed as uint64
+ * (cx+1) | (cy+1) << 21 | (cz+1) << 42 with c in [-1, n-1] per axis (the
+ * dual cells of Sec. 2.2); point ids are ordered by (cz, cy, cx). */
+sn_status sn_mesh_cells(const sn_mesh *m, const uint64_t **cells);
+
 /* Copies the arrays above into caller-allocated host buffers (any may be NULL)
  * with the layouts of sn_mesh_device_arrays; waits for the mesh's stream.
  * Returns SN_ETIMEOUT if a smoothing launch gave up a bounded wait. */

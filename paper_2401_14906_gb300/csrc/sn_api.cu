@@ -519,6 +519,13 @@ sn_status sn_mesh_face_masks(const sn_mesh *m, const uint8_t **face_masks)
     return SN_OK;
 }
 
+sn_status sn_mesh_cells(const sn_mesh *m, const uint64_t **cells)
+{
+    if (!m || !cells) return fail(SN_EINVAL, "mesh or output is NULL");
+    *cells = m->a.cells;
+    return SN_OK;
+}
+
 sn_status sn_mesh_copy_to_host(const sn_mesh *m, float *points, int32_t *quads, void *quad_labels,
                                int64_t *stencil_offsets, int32_t *stencil_ids, float *offsets)
 {

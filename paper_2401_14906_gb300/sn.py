@@ -47,6 +47,7 @@ SIGNATURES = {
     "sn_mesh_counts": (ctypes.c_int, [_P, _I64P, _I64P, _I64P]),
     "sn_mesh_device_arrays": (ctypes.c_int, [_P] + [ctypes.POINTER(_P)] * 6),
     "sn_mesh_face_masks": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "sn_mesh_cells": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
     "sn_mesh_copy_to_host": (ctypes.c_int, [_P] + [_P] * 6),
     "sn_free": (None, [_P]),
     "sn_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -254,6 +255,17 @@ def sn_mesh_device_arrays(mesh: Mesh):
     _check(load().sn_mesh_face_masks(mesh.handle, ctypes.byref(fm)))
     out["face_masks"] = torch.as_tensor(_CudaArray(fm.value, (n,), "|u1"), device="cuda")
     return out
+
+
+def sn_mesh_cells(mesh: Mesh):
+    """Each point's generating cell as a borrowed int64 tensor (n_points, 3) of (cx, cy, cz), unpacked on the device."""
+    torch = _torch()
+    p = ctypes.c_void_p()
+    _check(load().sn_mesh_cells(mesh.handle, ctypes.byref(p)))
+    n, _, _ = sn_mesh_counts(mesh)
+    packed = torch.as_tensor(_CudaArray(p.value, (n,), "<i8"), device="cuda")
+    m21 = (1 << 21) - 1
+    return torch.stack([(packed & m21) - 1, ((packed >> 21) & m21) - 1, ((packed >> 42) & m21) - 1], dim=1)
 
 
 def sn_mesh_face_masks_host(mesh: Mesh):
