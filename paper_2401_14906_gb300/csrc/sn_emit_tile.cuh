@@ -8,13 +8,12 @@
 namespace sn {
 namespace dev {
 
-constexpr int kTileRows = 16;  // cell rows per tile of the single-map kernel
+constexpr int kTileRows = 24;  // cell rows per tile of the single-map kernel
 constexpr int kTileMaxW = 64;  // rows of up to 2047 cells; wider rows use the per-row kernel
-constexpr int kListCap = 2048; // list entries per pass
 
 // shared-memory carve-up, in 4-byte words; every array starts on 16 bytes
 struct TileSmem {
-    int bar, P, planes, pre, base, F, dpre, qpre, soff, qoff, list, total;
+    int bar, P, planes, pre, base, F, dpre, qpre, soff, qoff, total;
     __host__ __device__ static int up4(int v) { return (v + 3) & ~3; }
     __host__ __device__ TileSmem(int ty, int W, int WS)
     {
@@ -29,10 +28,20 @@ struct TileSmem {
         qpre = dpre + up4(ty * W);             // [ty][W] quads before the word
         soff = qpre + up4(ty * W);             // [ty] int64 first stencil entry of the row
         qoff = soff + 2 * ty;                  // [ty] int64 first quad of the sample row
-        list = qoff + 2 * ty;                  // [kListCap]
-        total = list + kListCap;
+        total = qoff + 2 * ty;
     }
 };
+
+// position of the set bit of `word` with `nth` set bits below it (nth counted
+// from 0); 31 when the word has no more than nth set bits
+__device__ __forceinline__ int nth_bit(uint32_t word, int nth)
+{
+    int b = 0;
+#pragma unroll
+    for (int st = 16; st > 0; st >>= 1)
+        if (__popc(word & ((1u << (b + st)) - 1u)) <= nth) b += st;
+    return b;
+}
 
 // One tile (bx = run of cell rows, by = cz + 1) of the emission; called by the
 // single-map and the batched kernels.  Label rows are g.lp elements apart.
@@ -47,7 +56,7 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
 {
     extern __shared__ __align__(128) uint32_t sm[];
     const int TY = tg.ty, W = tg.W, WS = tg.WS, NS = tg.ns;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x, nwarps = nthr >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
     const int64_t ny = g.ny, nz = g.nz, ny1 = ny + 1, nz1 = nz + 1;
     const int64_t c0 = bx * TY; // first cy + 1 of the tile
     const int64_t czc = by;     // cz + 1
@@ -64,7 +73,6 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
     int32_t *sQpre = reinterpret_cast<int32_t *>(sm + L.qpre);
     int64_t *sSoff = reinterpret_cast<int64_t *>(sm + L.soff);
     int64_t *sQoff = reinterpret_cast<int64_t *>(sm + L.qoff);
-    uint32_t *sList = sm + L.list;
     const int64_t NP = __ldcg(&tot->n_points), NQ = __ldcg(&tot->n_quads), NS_ = __ldcg(&tot->n_stencil);
 
     // own cell row lr in [0, n): cy = c0 - 1 + lr; its sample row (cy, cz) exists iff cy >= 0 && cz >= 0
@@ -207,139 +215,132 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
         return sBase[slot] + sPre[slot * W + w] + __popc(sP[slot * WS + w] & ((1u << (p & 31)) - 1u));
     };
 
-    // ---- points and stencils, in id order
+    // ---- points and stencils, in id order.  Thread k takes point pbase + k and
+    // finds its cell itself: the own row by a search of the row offsets, the
+    // word by a search of the row's per-word prefixes, the bit as the n-th set
+    // bit of that word.
     const int last = slot_of(1, n - 1);
     const int32_t pbase = sBase[slot_of(1, 0)];
     const int32_t pend = sBase[last] + sPre[last * W + (W - 1)] + __popc(sP[last * WS + (W - 1)]);
     int32_t reach = 1;
-    for (int32_t win = pbase; win < pend; win += kListCap) {
-        __syncthreads();
-        for (int lr = warp; lr < n; lr += nwarps) {
-            const int so = slot_of(1, lr);
-            for (int w = lane; w < W; w += 32) {
-                uint32_t bits = sP[so * WS + w];
-                int32_t idx = sBase[so] + sPre[so * W + w];
-                while (bits) {
-                    const int b = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    if (idx >= win && idx < win + kListCap)
-                        sList[idx - win] = ((uint32_t)lr << 24) | ((uint32_t)w << 5) | (uint32_t)b;
-                    ++idx;
-                }
-            }
+    for (int32_t id = pbase + tid; id < pend; id += nthr) {
+        int lr = 0;
+        for (int hi = n; hi - lr > 1;) { // the last own row whose first id is <= id
+            const int mid = (lr + hi) >> 1;
+            if (sBase[slot_of(1, mid)] <= id) lr = mid;
+            else hi = mid;
         }
-        __syncthreads();
-        const int cnt = (pend - win) < kListCap ? (pend - win) : kListCap;
-        for (int k = tid; k < cnt; k += nthr) {
-            const uint32_t e = sList[k];
-            const int lr = (int)(e >> 24), w = (int)((e >> 5) & 0x7ffffu), b = (int)(e & 31u);
-            const int32_t id = win + k;
-            if (id < 0 || id >= NP) continue;
-            const uint32_t lt = (1u << b) - 1u;
-            const int64_t p = (int64_t)w * 32 + b;
-            const int64_t cx = p - 1, cy = c0 - 1 + lr;
-            float *pt = m.points + 3 * (int64_t)id;
-            pt[0] = m.lut_x[cx + 1].x;
-            pt[1] = m.lut_y[cy + 1].x;
-            pt[2] = m.lut_z[cz + 1].x;
-            float *of = m.offsets + 3 * (int64_t)id;
-            of[0] = 0.f;
-            of[1] = 0.f;
-            of[2] = 0.f;
-            m.cells[id] = (uint64_t)(cx + 1) | ((uint64_t)(cy + 1) << 21) | ((uint64_t)(cz + 1) << 42);
-            uint32_t mask = 0;
-            int64_t so = sSoff[lr] + sDpre[lr * W + w];
-#pragma unroll
-            for (int f = 0; f < 6; ++f) {
-                const uint32_t fw = sF[(lr * 6 + f) * W + w];
-                so += __popc(fw & lt);
-                mask |= ((fw >> b) & 1u) << f;
-            }
-            m.face_mask[id] = (uint8_t)mask;
-            m.sten_off[id] = so;
-            if (so < 0 || so + __popc(mask) > NS_) continue;
-            int32_t *dst = m.sten_ids + so;
-            if (mask & 1u) *dst++ = id - 1;
-            if (mask & 2u) *dst++ = id + 1;
-            uint32_t dist[4] = {0u, 0u, 0u, 0u};
-            const int nbs[4] = {slot_of(1, lr - 1), slot_of(1, lr + 1), slot_of(0, lr), slot_of(2, lr)};
-#pragma unroll
-            for (int f = 2; f < 6; ++f)
-                if ((mask >> f) & 1u) {
-                    const int32_t nb = rank(nbs[f - 2], p);
-                    *dst++ = nb;
-                    const int32_t d = nb > id ? nb - id : id - nb;
-                    reach = d > reach ? d : reach;
-                    dist[f - 2] = (uint32_t)d & 0x7fffu;
-                }
-            m.nbr[id] = make_uint2(dist[0] | ((mask & 1u) << 15) | (dist[1] << 16) | (((mask >> 1) & 1u) << 31),
-                                   dist[2] | (dist[3] << 16));
+        const int sr = slot_of(1, lr);
+        const int32_t r = id - sBase[sr];
+        int w = 0;
+        for (int hi = W; hi - w > 1;) { // the last word of the row with at most r points before it
+            const int mid = (w + hi) >> 1;
+            if (sPre[sr * W + mid] <= r) w = mid;
+            else hi = mid;
         }
+        const int b = nth_bit(sP[sr * WS + w], r - sPre[sr * W + w]);
+        if (id < 0 || id >= NP) continue;
+        const uint32_t lt = (1u << b) - 1u;
+        const int64_t p = (int64_t)w * 32 + b;
+        const int64_t cx = p - 1, cy = c0 - 1 + lr;
+        float *pt = m.points + 3 * (int64_t)id;
+        pt[0] = m.lut_x[cx + 1].x;
+        pt[1] = m.lut_y[cy + 1].x;
+        pt[2] = m.lut_z[cz + 1].x;
+        float *of = m.offsets + 3 * (int64_t)id;
+        of[0] = 0.f;
+        of[1] = 0.f;
+        of[2] = 0.f;
+        m.cells[id] = (uint64_t)(cx + 1) | ((uint64_t)(cy + 1) << 21) | ((uint64_t)(cz + 1) << 42);
+        uint32_t mask = 0;
+        int64_t so = sSoff[lr] + sDpre[lr * W + w];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const uint32_t fw = sF[(lr * 6 + f) * W + w];
+            so += __popc(fw & lt);
+            mask |= ((fw >> b) & 1u) << f;
+        }
+        m.face_mask[id] = (uint8_t)mask;
+        m.sten_off[id] = so;
+        if (so < 0 || so + __popc(mask) > NS_) continue;
+        int32_t *dst = m.sten_ids + so;
+        if (mask & 1u) *dst++ = id - 1;
+        if (mask & 2u) *dst++ = id + 1;
+        uint32_t dist[4] = {0u, 0u, 0u, 0u};
+        const int nbs[4] = {slot_of(1, lr - 1), slot_of(1, lr + 1), slot_of(0, lr), slot_of(2, lr)};
+#pragma unroll
+        for (int f = 2; f < 6; ++f)
+            if ((mask >> f) & 1u) {
+                const int32_t nb = rank(nbs[f - 2], p);
+                *dst++ = nb;
+                const int32_t d = nb > id ? nb - id : id - nb;
+                reach = d > reach ? d : reach;
+                dist[f - 2] = (uint32_t)d & 0x7fffu;
+            }
+        m.nbr[id] = make_uint2(dist[0] | ((mask & 1u) << 15) | (dist[1] << 16) | (((mask >> 1) & 1u) << 31),
+                               dist[2] | (dist[3] << 16));
     }
     reach = (int32_t)__reduce_max_sync(kFull, (unsigned)reach);
     if (lane == 0 && reach > 1) atomicMax(m.meta, reach);
 
-    // ---- quads of sample rows (cy, cz), cy = c0 - 1 + lr, in quad order
+    // ---- quads of sample rows (cy, cz), cy = c0 - 1 + lr, in quad order: within
+    // a word by bit, and at one bit x before y before z.  Thread k takes quad
+    // qbase + k and finds its row, word, bit and axis by searches as above.
     const int lr_first = (c0 == 0) ? 1 : 0; // cy = -1 has no sample row
     if (cz < 0 || lr_first >= n) return true;
     const int64_t qbase = sQoff[lr_first];
     const int64_t qend = sQoff[n - 1] + sQpre[(n - 1) * W + (W - 1)] + __popc(PL(0, 0, n - 1)[W - 1]) +
                          __popc(PL(0, 1, n - 1)[W - 1]) + __popc(PL(0, 2, n - 1)[W - 1]);
-    for (int64_t win = qbase; win < qend; win += kListCap) {
-        __syncthreads();
-        for (int lr = lr_first + warp; lr < n; lr += nwarps) {
-            const uint32_t *px = PL(0, 0, lr), *py = PL(0, 1, lr), *pz = PL(0, 2, lr);
-            for (int w = lane; w < W; w += 32) {
-                const uint32_t pw[3] = {px[w], py[w], pz[w]};
-                const int64_t w0 = sQoff[lr] + sQpre[lr * W + w];
-                // quad of (bit b, axis ax): quads of earlier bits, then earlier axes at b
+    for (int64_t q = qbase + tid; q < qend; q += nthr) {
+        int lr = lr_first;
+        for (int hi = n; hi - lr > 1;) {
+            const int mid = (lr + hi) >> 1;
+            if (sQoff[mid] <= q) lr = mid;
+            else hi = mid;
+        }
+        const int32_t r = (int32_t)(q - sQoff[lr]);
+        int w = 0;
+        for (int hi = W; hi - w > 1;) {
+            const int mid = (w + hi) >> 1;
+            if (sQpre[lr * W + mid] <= r) w = mid;
+            else hi = mid;
+        }
+        const uint32_t qx = PL(0, 0, lr)[w], qy = PL(0, 1, lr)[w], qz = PL(0, 2, lr)[w];
+        const int rr = r - sQpre[lr * W + w];
+        int b = 0; // the last bit with at most rr quads of the word below it
 #pragma unroll
-                for (int ax = 0; ax < 3; ++ax) {
-                    uint32_t bits = pw[ax];
-                    while (bits) {
-                        const int b = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const uint32_t lt = (1u << b) - 1u;
-                        int64_t idx = w0 + __popc(pw[0] & lt) + __popc(pw[1] & lt) + __popc(pw[2] & lt);
-                        if (ax > 0) idx += (pw[0] >> b) & 1u;
-                        if (ax > 1) idx += (pw[1] >> b) & 1u;
-                        if (idx >= win && idx < win + kListCap)
-                            sList[idx - win] =
-                                ((uint32_t)lr << 24) | ((uint32_t)ax << 22) | ((uint32_t)w << 5) | (uint32_t)b;
-                    }
-                }
-            }
+        for (int st = 16; st > 0; st >>= 1) {
+            const uint32_t mk = (1u << (b + st)) - 1u;
+            if (__popc(qx & mk) + __popc(qy & mk) + __popc(qz & mk) <= rr) b += st;
         }
-        __syncthreads();
-        const int cnt = (int)((qend - win) < kListCap ? (qend - win) : kListCap);
-        for (int k = tid; k < cnt; k += nthr) {
-            const uint32_t e = sList[k];
-            const int lr = (int)(e >> 24), ax = (int)((e >> 22) & 3u), w = (int)((e >> 5) & 0x1ffffu),
-                      b = (int)(e & 31u);
-            const int64_t q = win + k;
-            if (q < 0 || q >= NQ) continue;
-            const int64_t i = (int64_t)w * 32 + b;
-            const int64_t j = c0 - 1 + lr;
-            const T *row = lab + (j + ny * cz) * g.lp;
-            // cell rows: 00 = (cy, cz), m0 = (cy-1, cz), 0m = (cy, cz-1), mm = (cy-1, cz-1)
-            const int s00 = slot_of(1, lr), sm0 = slot_of(1, lr - 1), s0m = slot_of(0, lr), smm = slot_of(0, lr - 1);
-            int4 v;
-            int64_t d1;
-            if (ax == 0) {
-                v = make_int4(rank(smm, i + 1), rank(s0m, i + 1), rank(s00, i + 1), rank(sm0, i + 1));
-                d1 = 1;
-            } else if (ax == 1) {
-                v = make_int4(rank(s0m, i), rank(s00, i), rank(s00, i + 1), rank(s0m, i + 1));
-                d1 = g.lp;
-            } else {
-                v = make_int4(rank(sm0, i), rank(sm0, i + 1), rank(s00, i + 1), rank(s00, i));
-                d1 = g.lp * ny;
-            }
-            reinterpret_cast<int4 *>(m.quads)[q] = v;
-            T *ql = reinterpret_cast<T *>(m.quad_labels) + 2 * q;
-            ql[0] = (T)kappa<MODE>(c, ldlab(row, i));
-            ql[1] = (T)kappa<MODE>(c, ldlab(row, i + d1));
+        const uint32_t below = (1u << b) - 1u;
+        int k = rr - (__popc(qx & below) + __popc(qy & below) + __popc(qz & below));
+        const int hx = (int)((qx >> b) & 1u), hy = (int)((qy >> b) & 1u);
+        int ax = 2;
+        if (hx && k == 0) ax = 0;
+        else if (hy && k - hx == 0) ax = 1;
+        if (q < 0 || q >= NQ) continue;
+        const int64_t i = (int64_t)w * 32 + b;
+        const int64_t j = c0 - 1 + lr;
+        const T *row = lab + (j + ny * cz) * g.lp;
+        // cell rows: 00 = (cy, cz), m0 = (cy-1, cz), 0m = (cy, cz-1), mm = (cy-1, cz-1)
+        const int s00 = slot_of(1, lr), sm0 = slot_of(1, lr - 1), s0m = slot_of(0, lr), smm = slot_of(0, lr - 1);
+        int4 v;
+        int64_t d1;
+        if (ax == 0) {
+            v = make_int4(rank(smm, i + 1), rank(s0m, i + 1), rank(s00, i + 1), rank(sm0, i + 1));
+            d1 = 1;
+        } else if (ax == 1) {
+            v = make_int4(rank(s0m, i), rank(s00, i), rank(s00, i + 1), rank(s0m, i + 1));
+            d1 = g.lp;
+        } else {
+            v = make_int4(rank(sm0, i), rank(sm0, i + 1), rank(s00, i + 1), rank(s00, i));
+            d1 = g.lp * ny;
         }
+        reinterpret_cast<int4 *>(m.quads)[q] = v;
+        T *ql = reinterpret_cast<T *>(m.quad_labels) + 2 * q;
+        ql[0] = (T)kappa<MODE>(c, ldlab(row, i));
+        ql[1] = (T)kappa<MODE>(c, ldlab(row, i + d1));
     }
     return true;
 }
