@@ -12,9 +12,9 @@
 // cy..cy+n of slices cz and cz+1 are contiguous runs of rows in global memory;
 // one thread copies each run into shared memory with a bulk (TMA) copy.  The
 // tile then derives its face planes (one thread per word) and per-word
-// popcount prefixes (one thread per row), lists its points and quads in
-// canonical order (list index = id minus the tile's first id) and gives each
-// to one thread.
+// popcount prefixes (one thread per row).  Each thread then takes one point
+// (quad) id of the tile and finds the cell (edge) it belongs to by binary
+// searches of the row offsets, the row's per-word prefixes and the word's bits.
 #include "sn_emit_tile.cuh"
 
 namespace sn {
