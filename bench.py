@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "synthetic"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-learned", action="store_true",
+                   help="skip the learned-proposal comparison (plain smoothing vs proposal + corrections)")
     p.add_argument("--cpu-slab", type=int, default=0, help="z-slices of the map the oracle baseline runs on")
     p.add_argument("--label-sweep", action="store_true",
                    help="time extract + smooth with the first k of 128 sphere labels selected, k = 1..128")
@@ -412,6 +414,8 @@ def run_ours(args):
                               "frac": alg_total / path_time / 1e9 / peak},
             "kernels": kernels, "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clocks, "e2e": e2e}
+    if world == 1 and not args.no_learned:
+        line["learned"] = learned_comparison(w, args.steps)
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -419,6 +423,24 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def learned_comparison(w, repeats):
+    """Plain smoothing (the step's iteration count) vs the learned proposal + k correction sweeps on the
+    bench map, with the committed trained parameters: device times and the largest offset difference."""
+    from paper_2401_14906_gb300 import proposal
+    if not os.path.exists(proposal.PROPOSAL_PARAMS):
+        return {"unavailable": "no trained parameters (python -m paper_2401_14906_gb300.proposal)"}
+    L = proposal.load_learner()
+    r = proposal.evaluate(L, w.labels, w.spacing, w.iterations, w.relaxation, w.constraint,
+                          corrections=(0, 1, 2, 4), repeats=max(3, repeats))
+    L.free()
+    target = {"max_err_vox": 1e-3, "speedup_vs_plain": 2.0}
+    met = [c for c in r["learned"]
+           if c["max_err_vox"] <= target["max_err_vox"] and (c["speedup"] or 0) >= target["speedup_vs_plain"]]
+    return {"plain_ms": r["ms_plain"], "iterations": r["iterations"], "proposals": r["learned"],
+            "target": target, "met": bool(met),
+            "model": "MLP 32-64-64-3 BF16 (tensor cores), trained on 200 seeded 256^3 maps"}
 
 
 def run_label_sweep(args):

@@ -169,6 +169,79 @@ sn_status sn_triangulate(sn_mesh *m, sn_tri_method method);
 /* Borrowed device pointer to the triangles (NULL before sn_triangulate). */
 sn_status sn_mesh_triangles(const sn_mesh *m, const int32_t **triangles);
 
+/*
+ * Learned smoothing proposal.  Not in the paper: a multilayer perceptron
+ * predicts from each point's stencil and constraint box the offset that the
+ * plain smoother (Sec. 2.2 Eq. 1) reaches after its full iteration count; a
+ * few plain correction sweeps and the constraint clamp follow.  The plain
+ * smoother generates the training data and stays the reference the proposal
+ * is measured against.
+ *
+ * Model: features x (SN_LEARN_FEATURES = 32 per point, BF16) -> 64 -> 64 -> 3,
+ * ReLU after the two hidden layers, y = W x + b per layer; weights and hidden
+ * activations BF16, FP32 accumulation (tensor cores), FP32 biases and output.
+ * Features of point i, by slot:
+ *   0-2   s_i = sum of the unit steps towards i's stencil neighbours
+ *   3     number of stencil neighbours
+ *   4-9   1 if face f (-x,+x,-y,+y,-z,+z) is in the stencil, else 0
+ *   10-27 s_j of the neighbour j across face f (slots 10+3f..12+3f), 0 if none
+ *   28    d/2 (the box half-width, voxel units) rounded to BF16
+ *   29-31 0
+ * Parameters (FP32 host or device vector of SN_LEARN_PARAMS values, in this
+ * order): W1 [64][32], b1 [64], W2 [64][64], b2 [64], W3 [3][64], b3 [3].
+ * Training minimises the mean squared error of the offset (voxel units) by
+ * AdamW (beta1 0.9, beta2 0.999, eps 1e-8, decoupled decay on W1, W2, W3 only).
+ *
+ * A learner owns its parameters, AdamW moments and training examples in
+ * device memory and works on the stream given at creation.  Errors: SN_EINVAL
+ * (NULL arguments, sizes < 0 or > what the learner holds, non-finite or
+ * negative rates), SN_ENOMEM, SN_ECUDA; sn_last_error() has the detail.
+ */
+#define SN_LEARN_FEATURES 32
+#define SN_LEARN_PARAMS 6467
+typedef struct sn_learner sn_learner;
+
+/* A learner with all parameters zero and no examples. */
+sn_status sn_learner_create(void *cuda_stream, sn_learner **out);
+void sn_learner_free(sn_learner *l);
+/* Copy the parameters in (host float [SN_LEARN_PARAMS]; resets the AdamW
+ * moments and step count) or out (returns after the copy has completed). */
+sn_status sn_learner_set_params(sn_learner *l, const float *params);
+sn_status sn_learner_get_params(const sn_learner *l, float *params);
+/* Append one example per point of a smoothed mesh: its features for the given
+ * constraint distance and, as the target, the mesh's current offsets
+ * (voxel units, as sn_smooth left them). */
+sn_status sn_learner_add_examples(sn_learner *l, const sn_mesh *m, float constraint_distance);
+sn_status sn_learner_n_examples(const sn_learner *l, int64_t *n);
+/* `epochs` passes over the examples in minibatches of `batch` (the last one of
+ * a pass may be smaller), each followed by one AdamW step with learning rate
+ * lr and decay weight_decay.  Each pass visits the examples in the order
+ * k -> (a k + c) mod n with a coprime to n, a and c drawn from `seed` and the
+ * pass number.  *last_loss (may be NULL) receives the mean squared error of
+ * the last minibatch before its step. */
+sn_status sn_learner_train(sn_learner *l, int epochs, int64_t batch, float lr, float weight_decay, uint64_t seed,
+                           float *last_loss);
+/* The proposal and corrections on a mesh: offsets = clamp(MLP(features)),
+ * then `corrections` plain sweeps (relaxation, constraint as for sn_smooth_ex)
+ * from there; the world positions follow, as after sn_smooth. */
+sn_status sn_smooth_learned(sn_mesh *m, const sn_learner *l, int corrections, float relaxation,
+                            float constraint_distance, sn_constraint constraint);
+
+/* Building blocks, on caller-owned device arrays, enqueued on the learner's
+ * stream (sn_learn_features: on the mesh's stream):
+ *   sn_learn_features  features of every point, uint16 BF16 bits [n_points][32];
+ *   sn_learn_forward   y [n][3] (FP32) = MLP(x) for x [n][32] BF16 bits;
+ *   sn_learn_gradient  adds the gradient of the mean squared error of the n
+ *                      rows (x [n][32], targets t [n][3] FP32) to grads (FP32
+ *                      [SN_LEARN_PARAMS]) and its squared-error sum to *sse
+ *                      (device float);
+ *   sn_learner_step    one AdamW step of the learner with the gradient grads. */
+sn_status sn_learn_features(const sn_mesh *m, float constraint_distance, uint16_t *features);
+sn_status sn_learn_forward(const sn_learner *l, const uint16_t *x, int64_t n, float *y);
+sn_status sn_learn_gradient(const sn_learner *l, const uint16_t *x, const float *t, int64_t n, float *grads,
+                            float *sse);
+sn_status sn_learner_step(sn_learner *l, const float *grads, float lr, float weight_decay);
+
 /* Output sizes: points, quads, stencil entries (sum of stencil lengths). */
 sn_status sn_mesh_counts(const sn_mesh *m, int64_t *n_points, int64_t *n_quads, int64_t *n_stencil);
 

@@ -152,3 +152,45 @@ def adamw(params, grads, m, v, t, lr, weight_decay, beta1=0.9, beta2=0.999, eps=
     vhat = v / (1.0 - beta2 ** t)
     p = p - lr * (mhat / (np.sqrt(vhat) + eps) + weight_decay * weight_mask() * p)
     return p, m, v
+
+
+def smooth_from(stencil_offsets, stencil_ids, face_masks, o0, iterations, relaxation, constraint_distance,
+                sphere=False):
+    """Jacobi sweeps of Eq. 1 starting from the offsets o0 (n, 3), voxel units, FP64.
+
+    Each sweep reads every offset from the previous buffer (the double buffer of
+    Sec. 2.4): o_i <- clamp(o_i + lambda / N_i * sum_j (u_ij + o_j - o_i)), the
+    clamp a box of half-width d/2 per axis or (sphere) a ball of radius d/2."""
+    so = np.asarray(stencil_offsets, dtype=np.int64)
+    ids = np.asarray(stencil_ids, dtype=np.int64)
+    fm = np.asarray(face_masks, dtype=np.int64)
+    n = fm.size
+    h = 0.5 * float(np.float32(constraint_distance))
+    lam = float(np.float32(relaxation))
+    # (point, neighbour, unit step) triples in stencil order
+    rows, cols, steps = [], [], []
+    for i in range(n):
+        k = so[i]
+        for f in range(6):
+            if (fm[i] >> f) & 1:
+                rows.append(i)
+                cols.append(ids[k])
+                steps.append(UNIT[f])
+                k += 1
+    rows, cols = np.array(rows, dtype=np.int64), np.array(cols, dtype=np.int64)
+    steps = np.array(steps, dtype=np.float64).reshape(-1, 3)
+    deg = np.bincount(rows, minlength=n).astype(np.float64)
+    o = np.array(o0, dtype=np.float64).reshape(n, 3)
+    for _ in range(int(iterations)):
+        acc = np.zeros((n, 3))
+        np.add.at(acc, rows, steps + o[cols] - o[rows])
+        scale = np.where(deg > 0, lam / np.maximum(deg, 1.0), 0.0)
+        new = o + scale[:, None] * acc
+        if sphere:
+            r = np.sqrt((new * new).sum(axis=1))
+            f = np.where(r > h, h / np.where(r > 0, r, 1.0), 1.0)
+            new = new * f[:, None]
+        else:
+            new = np.clip(new, -h, h)
+        o = new
+    return o

@@ -28,6 +28,18 @@ struct sn_mesh {
     cudaMemPool_t pool;
 };
 
+struct sn_learner {
+    int device;
+    cudaStream_t stream;
+    cudaMemPool_t pool;
+    float *params, *m1, *m2, *grads, *sse; // FP32 master parameters, AdamW moments, gradient, loss sum
+    uint16_t *wq;                          // BF16 copy of the parameters (the weights are used)
+    uint16_t *x;                           // examples: features [cap][32] BF16 bits
+    float *t;                              //           targets [cap][3]
+    int64_t n, cap;
+    int step;
+};
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -563,6 +575,293 @@ void sn_free(sn_mesh *m)
                   m->tris};
     for (void *p : ps) pool_free(p, m->stream);
     std::free(m);
+}
+
+} // extern "C"
+
+// ---------------------------------------------------------------- learner
+namespace {
+
+sn_status learner_check(const sn_learner *l)
+{
+    if (!l) return fail(SN_EINVAL, "learner is NULL");
+    return SN_OK;
+}
+
+uint64_t mix64(uint64_t z)
+{
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+uint64_t gcd64(uint64_t a, uint64_t b)
+{
+    while (b) {
+        const uint64_t r = a % b;
+        a = b;
+        b = r;
+    }
+    return a;
+}
+
+} // namespace
+
+extern "C" {
+
+sn_status sn_learner_create(void *cuda_stream, sn_learner **out)
+{
+    g_last_error.clear();
+    if (!out) return fail(SN_EINVAL, "output is NULL");
+    *out = nullptr;
+    sn_learner *l = (sn_learner *)std::calloc(1, sizeof(sn_learner));
+    if (!l) return fail(SN_ENOMEM, "host allocation failed");
+    l->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&l->device);
+    if (e == cudaSuccess) e = device_pool(l->device, &l->pool);
+    if (e != cudaSuccess) {
+        std::free(l);
+        return cuda_fail(e, "learner device");
+    }
+    const size_t pb = sizeof(float) * sn::kLearnParams;
+    struct {
+        void **p;
+        size_t bytes;
+    } al[] = {{(void **)&l->params, pb}, {(void **)&l->m1, pb}, {(void **)&l->m2, pb},
+              {(void **)&l->grads, pb},  {(void **)&l->sse, 256}, {(void **)&l->wq, sizeof(uint16_t) * sn::kLearnParams}};
+    for (auto &a : al) {
+        sn_status r = pool_alloc(a.p, a.bytes, l->pool, l->stream, "learner parameters");
+        if (r == SN_OK) {
+            e = cudaMemsetAsync(*a.p, 0, a.bytes, l->stream);
+            if (e != cudaSuccess) r = cuda_fail(e, "learner parameters");
+        }
+        if (r != SN_OK) {
+            sn_learner_free(l);
+            return r;
+        }
+    }
+    *out = l;
+    return SN_OK;
+}
+
+void sn_learner_free(sn_learner *l)
+{
+    if (!l) return;
+    void *ps[] = {l->params, l->m1, l->m2, l->grads, l->sse, l->wq, l->x, l->t};
+    for (void *p : ps) pool_free(p, l->stream);
+    std::free(l);
+}
+
+sn_status sn_learner_set_params(sn_learner *l, const float *params)
+{
+    g_last_error.clear();
+    if (sn_status r = learner_check(l)) return r;
+    if (!params) return fail(SN_EINVAL, "params is NULL");
+    const size_t pb = sizeof(float) * sn::kLearnParams;
+    cudaError_t e = cudaMemcpyAsync(l->params, params, pb, cudaMemcpyHostToDevice, l->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(l->m1, 0, pb, l->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(l->m2, 0, pb, l->stream);
+    if (e == cudaSuccess) e = sn::launch_learn_quantise(l->params, l->wq, l->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(l->stream); // the host array may go away on return
+    if (e != cudaSuccess) return cuda_fail(e, "set params");
+    l->step = 0;
+    return SN_OK;
+}
+
+sn_status sn_learner_get_params(const sn_learner *l, float *params)
+{
+    g_last_error.clear();
+    if (sn_status r = learner_check(l)) return r;
+    if (!params) return fail(SN_EINVAL, "params is NULL");
+    cudaError_t e =
+        cudaMemcpyAsync(params, l->params, sizeof(float) * sn::kLearnParams, cudaMemcpyDeviceToHost, l->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(l->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "get params");
+    return SN_OK;
+}
+
+sn_status sn_learn_features(const sn_mesh *m, float constraint_distance, uint16_t *features)
+{
+    g_last_error.clear();
+    if (!m || !features) return fail(SN_EINVAL, "mesh or features is NULL");
+    if (!std::isfinite(constraint_distance) || constraint_distance < 0.f)
+        return fail(SN_EINVAL, "constraint distance must be finite and >= 0");
+    cudaError_t e = sn::launch_learn_features(m->a, m->np, 0.5f * constraint_distance, features, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "features launch");
+    return SN_OK;
+}
+
+sn_status sn_learner_add_examples(sn_learner *l, const sn_mesh *m, float constraint_distance)
+{
+    g_last_error.clear();
+    if (sn_status r = learner_check(l)) return r;
+    if (!m) return fail(SN_EINVAL, "mesh is NULL");
+    if (!std::isfinite(constraint_distance) || constraint_distance < 0.f)
+        return fail(SN_EINVAL, "constraint distance must be finite and >= 0");
+    if (m->np == 0) return SN_OK;
+    // the mesh's work must be complete before the learner's stream reads it
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mesh stream");
+    const int64_t need = l->n + m->np;
+    if (need > l->cap) {
+        int64_t cap = l->cap ? l->cap : 1 << 20;
+        while (cap < need) cap *= 2;
+        uint16_t *x = nullptr;
+        float *t = nullptr;
+        sn_status r = pool_alloc((void **)&x, sizeof(uint16_t) * sn::kLearnFeatures * (size_t)cap, l->pool, l->stream,
+                                 "training features");
+        if (r == SN_OK)
+            r = pool_alloc((void **)&t, sizeof(float) * 3 * (size_t)cap, l->pool, l->stream, "training targets");
+        if (r != SN_OK) {
+            pool_free(x, l->stream);
+            return r;
+        }
+        if (l->n) {
+            e = cudaMemcpyAsync(x, l->x, sizeof(uint16_t) * sn::kLearnFeatures * (size_t)l->n,
+                                cudaMemcpyDeviceToDevice, l->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(t, l->t, sizeof(float) * 3 * (size_t)l->n, cudaMemcpyDeviceToDevice, l->stream);
+            if (e != cudaSuccess) {
+                pool_free(x, l->stream);
+                pool_free(t, l->stream);
+                return cuda_fail(e, "grow examples");
+            }
+        }
+        pool_free(l->x, l->stream);
+        pool_free(l->t, l->stream);
+        l->x = x;
+        l->t = t;
+        l->cap = cap;
+    }
+    e = sn::launch_learn_features(m->a, m->np, 0.5f * constraint_distance, l->x + sn::kLearnFeatures * l->n,
+                                  l->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(l->t + 3 * l->n, m->a.offsets, sizeof(float) * 3 * (size_t)m->np,
+                            cudaMemcpyDeviceToDevice, l->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "add examples");
+    l->n = need;
+    return SN_OK;
+}
+
+sn_status sn_learner_n_examples(const sn_learner *l, int64_t *n)
+{
+    if (sn_status r = learner_check(l)) return r;
+    if (!n) return fail(SN_EINVAL, "output is NULL");
+    *n = l->n;
+    return SN_OK;
+}
+
+sn_status sn_learn_forward(const sn_learner *l, const uint16_t *x, int64_t n, float *y)
+{
+    g_last_error.clear();
+    if (sn_status r = learner_check(l)) return r;
+    if (n < 0 || (n > 0 && (!x || !y))) return fail(SN_EINVAL, "bad rows or NULL array");
+    cudaError_t e = sn::launch_learn_forward(l->wq, l->params, x, n, y, l->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    return SN_OK;
+}
+
+sn_status sn_learn_gradient(const sn_learner *l, const uint16_t *x, const float *t, int64_t n, float *grads,
+                            float *sse)
+{
+    g_last_error.clear();
+    if (sn_status r = learner_check(l)) return r;
+    if (n < 0 || !grads || !sse || (n > 0 && (!x || !t))) return fail(SN_EINVAL, "bad rows or NULL array");
+    cudaError_t e = sn::launch_learn_grad(l->wq, l->params, x, t, n > 0 ? n : 1, 0, n, 1, 0, grads, sse, l->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "gradient launch");
+    return SN_OK;
+}
+
+sn_status sn_learner_step(sn_learner *l, const float *grads, float lr, float weight_decay)
+{
+    g_last_error.clear();
+    if (sn_status r = learner_check(l)) return r;
+    if (!grads) return fail(SN_EINVAL, "grads is NULL");
+    if (!std::isfinite(lr) || lr < 0.f || !std::isfinite(weight_decay) || weight_decay < 0.f)
+        return fail(SN_EINVAL, "learning rate and decay must be finite and >= 0");
+    cudaError_t e = sn::launch_learn_adamw(l->params, l->m1, l->m2, grads, l->wq, lr, weight_decay, l->step + 1,
+                                           l->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "AdamW launch");
+    ++l->step;
+    return SN_OK;
+}
+
+sn_status sn_learner_train(sn_learner *l, int epochs, int64_t batch, float lr, float weight_decay, uint64_t seed,
+                           float *last_loss)
+{
+    g_last_error.clear();
+    if (sn_status r = learner_check(l)) return r;
+    if (epochs < 0 || batch < 1) return fail(SN_EINVAL, "epochs must be >= 0 and batch >= 1");
+    if (!std::isfinite(lr) || lr < 0.f || !std::isfinite(weight_decay) || weight_decay < 0.f)
+        return fail(SN_EINVAL, "learning rate and decay must be finite and >= 0");
+    if (l->n == 0) return fail(SN_EINVAL, "the learner has no examples");
+    const uint64_t n = (uint64_t)l->n;
+    int64_t last = 0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        // visiting order k -> (a k + c) mod n, a coprime to n and below 2^31
+        uint64_t a = (mix64(seed ^ (0x51ed27ull * (uint64_t)(ep + 1))) % 0x7fffffffull) | 1ull;
+        while (gcd64(a % n ? a % n : n, n) != 1 && n > 1) a += 2;
+        const uint64_t c = mix64(seed + 0x9e37ull * (uint64_t)(ep + 1)) % n;
+        for (int64_t s0 = 0; s0 < l->n; s0 += batch) {
+            const int64_t nb = std::min<int64_t>(batch, l->n - s0);
+            cudaError_t e = cudaMemsetAsync(l->grads, 0, sizeof(float) * sn::kLearnParams, l->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(l->sse, 0, sizeof(float), l->stream);
+            if (e == cudaSuccess)
+                e = sn::launch_learn_grad(l->wq, l->params, l->x, l->t, l->n, s0, nb, a % n ? a % n : 1, c, l->grads,
+                                          l->sse, l->stream);
+            if (e == cudaSuccess)
+                e = sn::launch_learn_adamw(l->params, l->m1, l->m2, l->grads, l->wq, lr, weight_decay, l->step + 1,
+                                           l->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "training launch");
+            ++l->step;
+            last = nb;
+        }
+    }
+    if (last_loss) {
+        float sse = 0.f;
+        cudaError_t e = cudaMemcpyAsync(&sse, l->sse, sizeof(float), cudaMemcpyDeviceToHost, l->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(l->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "loss read-back");
+        *last_loss = last ? sse / (3.f * (float)last) : 0.f;
+    }
+    return SN_OK;
+}
+
+sn_status sn_smooth_learned(sn_mesh *m, const sn_learner *l, int corrections, float relaxation,
+                            float constraint_distance, sn_constraint constraint)
+{
+    g_last_error.clear();
+    if (!m) return fail(SN_EINVAL, "mesh is NULL");
+    if (sn_status r = learner_check(l)) return r;
+    if (constraint != SN_CONSTRAINT_BOX && constraint != SN_CONSTRAINT_SPHERE)
+        return fail(SN_EINVAL, "unknown constraint");
+    if (corrections < 0) return fail(SN_EINVAL, "corrections must be >= 0");
+    if (!std::isfinite(relaxation) || relaxation < 0.f) return fail(SN_EINVAL, "relaxation must be finite and >= 0");
+    if (!std::isfinite(constraint_distance) || constraint_distance < 0.f)
+        return fail(SN_EINVAL, "constraint distance must be finite and >= 0");
+    if (m->np == 0) return SN_OK;
+    if (!m->smooth_scratch) {
+        sn_status r = pool_alloc((void **)&m->smooth_scratch, sizeof(float) * 3 * (size_t)m->np, m->pool, m->stream,
+                                 "smoothing buffer");
+        if (r != SN_OK) return r;
+    }
+    // the learner's parameters are written on its stream
+    cudaError_t e = cudaSuccess;
+    if (l->stream != m->stream) {
+        e = cudaStreamSynchronize(l->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "learner stream");
+    }
+    const float half = 0.5f * constraint_distance;
+    const int sphere = constraint == SN_CONSTRAINT_SPHERE;
+    // the proposal lands where an odd or even number of sweeps ends in m.offsets
+    float *start = (corrections % 2 == 1) ? m->smooth_scratch : m->a.offsets;
+    e = sn::launch_learn_propose(l->wq, l->params, m->a, start, m->np, half, sphere, m->stream);
+    if (e == cudaSuccess)
+        e = sn::launch_smooth_from(m->a, m->np, corrections, relaxation, half, sphere, start,
+                                   start == m->a.offsets ? m->smooth_scratch : m->a.offsets, m->spacing, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "learned smoothing launch");
+    return SN_OK;
 }
 
 } // extern "C"

@@ -129,6 +129,27 @@ cudaError_t launch_centre_lut(const MeshArrays &m, const int64_t dims[3], const 
 cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float relaxation, float half,
                           int sphere, float *scratch, const double spacing[3], cudaStream_t st);
 
+// Jacobi sweeps that start from the offsets already in `start` (3*np floats,
+// either m.offsets or scratch); the result ends in m.offsets and the world
+// positions in m.points.  iterations == 0 only writes the world positions.
+cudaError_t launch_smooth_from(const MeshArrays &m, int64_t np, int iterations, float relaxation, float half,
+                               int sphere, float *start, float *scratch, const double spacing[3], cudaStream_t st);
+
+// learned smoothing proposal (sn_learn.cu); parameters in the layout of sn.h
+constexpr int kLearnParams = 6467;
+constexpr int kLearnFeatures = 32;
+cudaError_t launch_learn_quantise(const float *params, uint16_t *wq, cudaStream_t st);
+cudaError_t launch_learn_features(const MeshArrays &m, int64_t np, float half, uint16_t *X, cudaStream_t st);
+cudaError_t launch_learn_forward(const uint16_t *wq, const float *params, const uint16_t *X, int64_t n, float *Y,
+                                 cudaStream_t st);
+cudaError_t launch_learn_propose(const uint16_t *wq, const float *params, const MeshArrays &m, float *out,
+                                 int64_t np, float half, int sphere, cudaStream_t st);
+cudaError_t launch_learn_grad(const uint16_t *wq, const float *params, const uint16_t *X, const float *T,
+                              int64_t total, int64_t start, int64_t n, uint64_t pa, uint64_t pc, float *grads,
+                              float *sse, cudaStream_t st);
+cudaError_t launch_learn_adamw(float *params, float *m1, float *m2, const float *grads, uint16_t *wq, float lr,
+                               float wd, int step, cudaStream_t st);
+
 // triangulation (sn_triangulate.cu): tris holds 6 * nq int32
 cudaError_t launch_triangulate(const MeshArrays &m, int64_t np, int64_t nq, int method, int32_t *tris,
                                cudaStream_t st);

@@ -28,6 +28,19 @@ __global__ void __launch_bounds__(256) k_centres(MeshArrays m, int64_t np)
     m.points[3 * i + 2] = m.lut_z[(c >> 42) & m21].x;
 }
 
+// world positions from the offsets in `o`
+__global__ void __launch_bounds__(256) k_world(MeshArrays m, const float *o, int64_t np, float spx, float spy,
+                                               float spz)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const uint64_t c = m.cells[i];
+    const uint64_t m21 = (1ull << 21) - 1ull;
+    m.points[3 * i + 0] = world(m.lut_x[c & m21], spx, o[3 * i + 0]);
+    m.points[3 * i + 1] = world(m.lut_y[(c >> 21) & m21], spy, o[3 * i + 1]);
+    m.points[3 * i + 2] = world(m.lut_z[(c >> 42) & m21], spz, o[3 * i + 2]);
+}
+
 } // namespace
 
 cudaError_t launch_centres(const MeshArrays &m, int64_t np, cudaStream_t st)
@@ -76,6 +89,61 @@ cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float
         ProfScope ps("k_smooth", st);
         k_smooth<<<blocks, kSweepThreads, 0, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        float *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    return cudaSuccess;
+}
+
+} // namespace sn
+
+namespace sn {
+
+cudaError_t launch_smooth_from(const MeshArrays &m, int64_t np, int iterations, float relaxation, float half,
+                               int sphere, float *start, float *scratch, const double spacing[3], cudaStream_t st)
+{
+    if (np == 0) return cudaSuccess;
+    if (iterations == 0) {
+        if (start != m.offsets) {
+            cudaError_t e = cudaMemcpyAsync(m.offsets, start, sizeof(float) * 3 * (size_t)np,
+                                            cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return e;
+        }
+        k_world<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(m, m.offsets, np, (float)spacing[0],
+                                                              (float)spacing[1], (float)spacing[2]);
+        return cudaGetLastError();
+    }
+    SweepArgs a;
+    a.nbr = m.nbr;
+    a.soff = m.sten_off;
+    a.sids = m.sten_ids;
+    a.fmask = m.face_mask;
+    a.meta = m.meta;
+    a.cells = m.cells;
+    a.lut_x = m.lut_x;
+    a.lut_y = m.lut_y;
+    a.lut_z = m.lut_z;
+    a.points = m.points;
+    a.np = np;
+    a.lam = relaxation;
+    a.h = half;
+    a.sphere = sphere;
+    a.spx = (float)spacing[0];
+    a.spy = (float)spacing[1];
+    a.spz = (float)spacing[2];
+    a.first = 0;
+    float *src = start;
+    float *dst = start == m.offsets ? scratch : m.offsets;
+    const unsigned blocks = (unsigned)((np + kSweepPoints - 1) / kSweepPoints);
+    for (int t = 0; t < iterations; ++t) {
+        a.oin = src;
+        a.oout = dst;
+        a.last = t == iterations - 1;
+        ProfScope ps("k_smooth", st);
+        k_smooth<<<blocks, kSweepThreads, 0, st>>>(a);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
         float *tmp = src;
         src = dst;
         dst = tmp;

@@ -54,6 +54,19 @@ SIGNATURES = {
     "sn_last_error": (ctypes.c_char_p, []),
     "sn_smooth_static": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                         _P, _P]),
+    "sn_learner_create": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "sn_learner_free": (None, [_P]),
+    "sn_learner_set_params": (ctypes.c_int, [_P, _P]),
+    "sn_learner_get_params": (ctypes.c_int, [_P, _P]),
+    "sn_learner_add_examples": (ctypes.c_int, [_P, _P, ctypes.c_float]),
+    "sn_learner_n_examples": (ctypes.c_int, [_P, _I64P]),
+    "sn_learner_train": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
+                                        ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)]),
+    "sn_smooth_learned": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_int]),
+    "sn_learn_features": (ctypes.c_int, [_P, ctypes.c_float, _P]),
+    "sn_learn_forward": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
+    "sn_learn_gradient": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
+    "sn_learner_step": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float]),
     "sn_profile_enable": (None, [ctypes.c_int]),
     "sn_profile_read": (ctypes.c_int, [ctypes.POINTER(sn_kernel_time), ctypes.c_int, ctypes.c_int]),
 }
@@ -295,3 +308,108 @@ def sn_profile_read(reset=False):
     buf = (sn_kernel_time * 64)()
     n = lib.sn_profile_read(buf, 64, 1 if reset else 0)
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n, 64))}
+
+
+# ------------------------------------------------------- learned proposal
+SN_LEARN_FEATURES, SN_LEARN_PARAMS = 32, 6467
+
+
+class Learner:
+    """Owner of an sn_learner* (parameters, AdamW state, examples on the device)."""
+
+    def __init__(self, stream=None):
+        out = ctypes.c_void_p()
+        _check(load().sn_learner_create(ctypes.c_void_p(_stream_handle(stream, True)), ctypes.byref(out)))
+        self._h = out
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("learner has been freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            load().sn_learner_free(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sn_learner_create(stream=None) -> Learner:
+    return Learner(stream)
+
+
+def sn_learner_set_params(learner: Learner, params):
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    if p.size != SN_LEARN_PARAMS:
+        raise ValueError(f"expected {SN_LEARN_PARAMS} parameters")
+    _check(load().sn_learner_set_params(learner.handle, ctypes.c_void_p(p.ctypes.data)))
+
+
+def sn_learner_get_params(learner: Learner):
+    p = np.empty(SN_LEARN_PARAMS, np.float32)
+    _check(load().sn_learner_get_params(learner.handle, ctypes.c_void_p(p.ctypes.data)))
+    return p
+
+
+def sn_learner_add_examples(learner: Learner, mesh: Mesh, constraint_distance=1.0):
+    _check(load().sn_learner_add_examples(learner.handle, mesh.handle, float(constraint_distance)))
+
+
+def sn_learner_n_examples(learner: Learner):
+    n = ctypes.c_int64()
+    _check(load().sn_learner_n_examples(learner.handle, ctypes.byref(n)))
+    return n.value
+
+
+def sn_learner_train(learner: Learner, epochs, batch, lr, weight_decay=0.0, seed=0):
+    """Returns the mean squared error of the last minibatch."""
+    loss = ctypes.c_float()
+    _check(load().sn_learner_train(learner.handle, int(epochs), int(batch), float(lr), float(weight_decay),
+                                   int(seed) & (2 ** 64 - 1), ctypes.byref(loss)))
+    return loss.value
+
+
+def sn_smooth_learned(mesh: Mesh, learner: Learner, corrections=2, relaxation=0.5, constraint_distance=1.0,
+                      sphere=False):
+    _check(load().sn_smooth_learned(mesh.handle, learner.handle, int(corrections), float(relaxation),
+                                    float(constraint_distance), SN_CONSTRAINT_SPHERE if sphere else SN_CONSTRAINT_BOX))
+
+
+def sn_learn_features(mesh: Mesh, constraint_distance=1.0):
+    """Features of every point: a device int16 tensor (n_points, 32) holding BF16 bit patterns."""
+    torch = _torch()
+    n, _, _ = sn_mesh_counts(mesh)
+    x = torch.empty((max(n, 1), SN_LEARN_FEATURES), dtype=torch.int16, device="cuda")
+    _check(load().sn_learn_features(mesh.handle, float(constraint_distance), ctypes.c_void_p(x.data_ptr())))
+    return x[:n]
+
+
+def sn_learn_forward(learner: Learner, x):
+    """y (n, 3) float32 device tensor = MLP(x) for device BF16-bit rows x (n, 32)."""
+    torch = _torch()
+    x = x.contiguous()
+    n = x.shape[0]
+    y = torch.empty((max(n, 1), 3), dtype=torch.float32, device="cuda")
+    _check(load().sn_learn_forward(learner.handle, ctypes.c_void_p(x.data_ptr()), n, ctypes.c_void_p(y.data_ptr())))
+    return y[:n]
+
+
+def sn_learn_gradient(learner: Learner, x, t):
+    """(gradient float32 device tensor (SN_LEARN_PARAMS,), sum of squared errors) for rows x, targets t (n, 3)."""
+    torch = _torch()
+    x, t = x.contiguous(), t.contiguous().float()
+    g = torch.zeros(SN_LEARN_PARAMS, dtype=torch.float32, device="cuda")
+    sse = torch.zeros(1, dtype=torch.float32, device="cuda")
+    _check(load().sn_learn_gradient(learner.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                    x.shape[0], ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(sse.data_ptr())))
+    return g, sse
+
+
+def sn_learner_step(learner: Learner, grads, lr, weight_decay=0.0):
+    _check(load().sn_learner_step(learner.handle, ctypes.c_void_p(grads.data_ptr()), float(lr), float(weight_decay)))

@@ -221,3 +221,26 @@ def test_adamw_two_scalar_steps_by_hand():
     mhat, vhat = m2 / (1 - 0.81), v2 / (1 - 0.999 ** 2)
     want = 0.85 - 0.1 * (mhat / np.sqrt(vhat) + 0.5 * 0.85)
     assert p[k] == pytest.approx(want, abs=1e-14)
+
+
+# ------------------------------------------------- smoothing from given offsets
+@pytest.mark.parametrize("sphere", [False, True])
+def test_smooth_from_zero_matches_the_c_oracle(sphere):
+    rng = np.random.default_rng(8)
+    lab = rng.integers(0, 3, size=(8, 9, 10)).astype(np.uint16)
+    m = oracle.extract(lab, spacing=(1.0, 2.0, 0.5))
+    off, _ = oracle.smooth(m, spacing=(1.0, 2.0, 0.5), iterations=7, relaxation=0.5, constraint=0.75, sphere=sphere)
+    o = learn.smooth_from(m.stencil_offsets, m.stencil_ids, m.face_masks, np.zeros((m.n_points, 3)), 7, 0.5, 0.75,
+                          sphere=sphere)
+    np.testing.assert_allclose(o, off, rtol=0, atol=1e-12)
+
+
+def test_smooth_from_splits_into_consecutive_runs():
+    rng = np.random.default_rng(9)
+    lab = rng.integers(0, 2, size=(7, 7, 7)).astype(np.uint8)
+    m = oracle.extract(lab)
+    args = (m.stencil_offsets, m.stencil_ids, m.face_masks)
+    o5 = learn.smooth_from(*args, np.zeros((m.n_points, 3)), 5, 0.4, 1.0)
+    o2 = learn.smooth_from(*args, np.zeros((m.n_points, 3)), 2, 0.4, 1.0)
+    o23 = learn.smooth_from(*args, o2, 3, 0.4, 1.0)
+    np.testing.assert_allclose(o23, o5, rtol=0, atol=1e-15)
