@@ -42,7 +42,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "synthetic"])
+    p.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5", "synthetic"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-learned", action="store_true",
@@ -486,12 +486,76 @@ def run_label_sweep(args):
     return 0
 
 
+def run_batch(args):
+    """The 256 seeded maps of uneven sizes (edges 32-256, uint8/uint16): a step is extract + 16 sweeps of every
+    map.  Timed with the host clock around the whole step (host work included) after a device sync, for the
+    batched call (parallel streams, one graph, tuned tile heights) and for a loop of single-map calls."""
+    import torch
+    import sn_synth
+    from paper_2401_14906_gb300 import build
+    build.build()
+    from paper_2401_14906_gb300 import sn
+    sn.load()
+    ws = sn_synth.config5_maps()
+    V = sum(w.voxels for w in ws)
+    labs = [to_device(w.labels) for w in ws]
+    it, lam, d = ws[0].iterations, ws[0].relaxation, ws[0].constraint
+
+    def batched():
+        ms = sn.sn_extract_smooth_batch(labs, iterations=it, relaxation=lam, constraint_distance=d)
+        torch.cuda.synchronize()
+        return ms
+
+    def looped():
+        ms = []
+        for t in labs:
+            m = sn.sn_extract(t)
+            sn.sn_smooth(m, it, lam, d)
+            ms.append(m)
+        torch.cuda.synchronize()
+        return ms
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            for m in fn():
+                m.free()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for m in fn():
+                m.free()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3 / args.steps
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    ms_batch = timed(batched)
+    clocks = sampler.stop()
+    ms_loop = timed(looped)
+    counts = [m.counts for m in batched()]
+    P = sum(c[0] for c in counts)
+    line = {"metric": METRIC, "value": V / (ms_batch / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8/u16+f32", "data": "synthetic",
+            "config": {"workload": "c5_256maps_edges32-256_u8u16", "maps": len(ws), "voxels": V, "points": P,
+                       "iterations": it, "timing": "host clock around each step (allocation, launches, waits)",
+                       "batched": "sn_extract_smooth_batch: 8 streams, one CUDA graph, tuned emission tiles",
+                       "single_map_loop_ms_per_step": ms_loop,
+                       "single_map_loop_gvoxels_s": V / (ms_loop / 1e3) / 1e9},
+            "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.label_sweep:
         return run_label_sweep(args)
+    if args.workload == "c5":
+        return run_batch(args)
     return run_ours(args)
 
 

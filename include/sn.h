@@ -170,6 +170,36 @@ sn_status sn_triangulate(sn_mesh *m, sn_tri_method method);
 sn_status sn_mesh_triangles(const sn_mesh *m, const int32_t **triangles);
 
 /*
+ * sn_extract_smooth_batch -- sn_extract (every value other than `background`
+ * selected) followed by sn_smooth for each of n_maps label maps of any sizes
+ * and label types.  Not in the paper: many small maps keep the GPU busy only
+ * when they run side by side, so the maps' counting passes run on parallel
+ * streams, one wait reads all totals back, the outputs are allocated exactly,
+ * and the emission and smoothing of every map are enqueued on parallel
+ * branches.
+ *   labels[i]   device or host pointer, map i (nz, ny, nx) x-fastest, type types[i]
+ *   dims        int64 [n_maps][3] (nx, ny, nz)
+ *   spacing, origin  double [n_maps][3], or NULL for 1 and 0
+ *   iterations, relaxation, constraint_distance  as for sn_smooth (box)
+ *   flags       SN_BATCH_GRAPH: capture the emission and smoothing of all maps
+ *               into one CUDA graph and launch it once;
+ *               SN_BATCH_TUNE: choose the emission tile height per (label
+ *               type, words per row, size class of rows and slices) by timing
+ *               the candidates 8/16/24/32 on the first map of each class
+ *               (cached for the process; results do not depend on it)
+ *   out         sn_mesh* [n_maps]: each mesh is what sn_extract + sn_smooth
+ *               give for that map, on cuda_stream, freed with sn_free.
+ * Returns after the work is enqueued.  On an error no mesh is returned.
+ * Errors: as sn_extract and sn_smooth.
+ */
+#define SN_BATCH_GRAPH 1
+#define SN_BATCH_TUNE 2
+sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, const sn_label_type *types,
+                                  const int64_t *dims, const double *spacing, const double *origin,
+                                  uint32_t background, int iterations, float relaxation, float constraint_distance,
+                                  int flags, void *cuda_stream, sn_mesh **out);
+
+/*
  * Learned smoothing proposal.  Not in the paper: a multilayer perceptron
  * predicts from each point's stencil and constraint box the offset that the
  * plain smoother (Sec. 2.2 Eq. 1) reaches after its full iteration count; a

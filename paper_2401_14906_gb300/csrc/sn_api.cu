@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "sn_internal.h"
@@ -138,6 +139,11 @@ void set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
 ProfScope::ProfScope(const char *name, cudaStream_t st) : name_(name), st_(st), a_(nullptr), b_(nullptr), on_(false)
 {
     if (!g_prof_on.load()) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st_, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return; // launches captured into a graph are not timed one by one
+    }
     if (cudaEventCreate(&a_) != cudaSuccess || cudaEventCreate(&b_) != cudaSuccess) {
         cudaGetLastError();
         return;
@@ -160,6 +166,281 @@ ProfScope::~ProfScope()
 }
 
 } // namespace sn
+
+namespace {
+
+// One map's extraction, split into the steps that the single-map call runs
+// back to back and the batched call interleaves across maps:
+//   job_prepare   checks, label copy, classifier, geometry, scratch
+//   job_count     Passes 1-3 and the scan (Sec. 2.3), totals copied to pinned memory
+//   (the caller waits for the stream)
+//   job_allocate  exact output allocation from the totals (end of Pass 3)
+//   job_emit      cell-centre tables and Pass 4
+//   job_release   scratch freed (stream-ordered), a mesh not handed out freed
+struct ExtractJob {
+    sn_label_type type = SN_U8;
+    int64_t dims[3] = {0, 0, 0};
+    double spacing[3] = {1, 1, 1}, origin[3] = {0, 0, 0};
+    int dev = 0;
+    cudaMemPool_t pool = nullptr;
+    const void *dlabels = nullptr;
+    sn::Classifier cls;
+    sn::Geometry g;
+    sn::ExtractScratch s;
+    sn::DevTotals *dtot = nullptr;
+    sn::DevTotals *htot = nullptr; // pinned
+    bool own_htot = false;
+    std::vector<void *> temps;
+    sn_mesh *mesh = nullptr;
+};
+
+sn_status job_prepare(ExtractJob &j, const void *labels, sn_label_type type, const int64_t dims[3],
+                      const double spacing[3], const double origin[3], const uint32_t *selected, int64_t n_selected,
+                      uint32_t background, cudaStream_t st)
+{
+    if (!labels) return fail(SN_EINVAL, "labels is NULL");
+    if (type != SN_U8 && type != SN_U16 && type != SN_U32) return fail(SN_EINVAL, "bad label type");
+    if (!dims || !spacing || !origin) return fail(SN_EINVAL, "dims, spacing or origin is NULL");
+    const int64_t kMaxDim = (1ll << 21) - 2;
+    for (int a = 0; a < 3; ++a) {
+        if (dims[a] < 1 || dims[a] > kMaxDim) return fail(SN_EINVAL, "dims must be in [1, 2^21-2]");
+        if (!finite_pos(spacing[a])) return fail(SN_EINVAL, "spacing must be finite and > 0");
+        if (!std::isfinite(origin[a])) return fail(SN_EINVAL, "origin must be finite");
+    }
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+    const int64_t V = nx * ny * nz;
+    if (V >= (1ll << 40)) return fail(SN_EINVAL, "nx*ny*nz must be < 2^40");
+    const uint64_t tmax = type == SN_U8 ? 0xffull : type == SN_U16 ? 0xffffull : 0xffffffffull;
+    if ((uint64_t)background > tmax) return fail(SN_EINVAL, "background does not fit the label type");
+    if (n_selected < 0 || (n_selected > 0 && !selected) || (selected && n_selected == 0))
+        return fail(SN_EINVAL, "selected/n_selected mismatch");
+    std::vector<uint32_t> sel;
+    if (selected) {
+        sel.assign(selected, selected + n_selected);
+        for (uint32_t v : sel) {
+            if ((uint64_t)v > tmax) return fail(SN_EINVAL, "a selected label does not fit the label type");
+            if (v == background) return fail(SN_EINVAL, "a selected label equals the background value");
+        }
+        std::sort(sel.begin(), sel.end());
+        sel.erase(std::unique(sel.begin(), sel.end()), sel.end());
+    }
+    j.type = type;
+    for (int a = 0; a < 3; ++a) {
+        j.dims[a] = dims[a];
+        j.spacing[a] = spacing[a];
+        j.origin[a] = origin[a];
+    }
+    cudaError_t e = cudaGetDevice(&j.dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    e = device_pool(j.dev, &j.pool);
+    if (e != cudaSuccess) return cuda_fail(e, "memory pool");
+    auto talloc = [&](void **p, size_t bytes, const char *what) -> sn_status {
+        sn_status r = pool_alloc(p, bytes, j.pool, st, what);
+        if (r == SN_OK) j.temps.push_back(*p);
+        return r;
+    };
+
+    // labels: in place when the device can read them, else one copy
+    const size_t lab_bytes = (size_t)V * (size_t)type;
+    j.dlabels = labels;
+    cudaPointerAttributes attr;
+    e = cudaPointerGetAttributes(&attr, labels);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        attr.type = cudaMemoryTypeUnregistered;
+    }
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
+        void *d = nullptr;
+        sn_status r = talloc(&d, lab_bytes, "label copy");
+        if (r != SN_OK) return r;
+        e = cudaMemcpyAsync(d, labels, lab_bytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "label copy");
+        j.dlabels = d;
+    }
+
+    // classifier (Sec. 3.1)
+    std::memset(&j.cls, 0, sizeof(j.cls));
+    j.cls.background = background;
+    j.cls.mode = sn::CLASS_ALL;
+    if (selected) {
+        const uint32_t vmax = sel.empty() ? 0u : sel.back();
+        if (vmax < (1u << 24)) {
+            j.cls.mode = sn::CLASS_BITMAP;
+            j.cls.nbits = vmax + 1u;
+            std::vector<uint32_t> bm((j.cls.nbits + 31) / 32, 0u);
+            for (uint32_t v : sel) bm[v >> 5] |= 1u << (v & 31u);
+            void *d = nullptr;
+            sn_status r = talloc(&d, bm.size() * 4, "label bitmap");
+            if (r != SN_OK) return r;
+            e = cudaMemcpyAsync(d, bm.data(), bm.size() * 4, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st); // bm is a local vector
+            if (e != cudaSuccess) return cuda_fail(e, "label bitmap copy");
+            j.cls.bitmap = (const uint32_t *)d;
+        } else {
+            j.cls.mode = sn::CLASS_SORTED;
+            j.cls.nsorted = (int64_t)sel.size();
+            void *d = nullptr;
+            sn_status r = talloc(&d, sel.size() * 4, "label list");
+            if (r != SN_OK) return r;
+            e = cudaMemcpyAsync(d, sel.data(), sel.size() * 4, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(e, "label list copy");
+            j.cls.sorted = (const uint32_t *)d;
+        }
+    }
+
+    sn::Geometry &g = j.g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.W = (nx + 1 + 31) / 32;
+    g.WS = (g.W + 3) / 4 * 4;
+    g.Rs = ny * nz;
+    g.Rc = (ny + 1) * (nz + 1);
+    g.lp = nx;
+    const int ntiles = (int)((g.Rc + sn::kScanTile - 1) / sn::kScanTile);
+
+    sn::ExtractScratch &s = j.s;
+    std::memset(&s, 0, sizeof(s));
+    struct {
+        void **p;
+        size_t bytes;
+        const char *what;
+    } plan[] = {
+        {(void **)&s.X, sizeof(uint32_t) * (size_t)(g.Rs * g.WS), "X plane"},
+        {(void **)&s.Y, sizeof(uint32_t) * (size_t)(g.Rs * g.WS), "Y plane"},
+        {(void **)&s.Z, sizeof(uint32_t) * (size_t)(g.Rs * g.WS), "Z plane"},
+        {(void **)&s.P, sizeof(uint32_t) * (size_t)(g.Rc * g.WS), "point plane"},
+        {(void **)&s.cntP, sizeof(int32_t) * (size_t)g.Rc, "point counts"},
+        {(void **)&s.cntS, sizeof(int32_t) * (size_t)g.Rc, "stencil counts"},
+        {(void **)&s.cntQ, sizeof(int32_t) * (size_t)g.Rc, "quad counts"},
+        {(void **)&s.offP, sizeof(int64_t) * (size_t)(g.Rc + 1), "point offsets"},
+        {(void **)&s.offS, sizeof(int64_t) * (size_t)(g.Rc + 1), "stencil offsets"},
+        {(void **)&s.offQ, sizeof(int64_t) * (size_t)(g.Rc + 1), "quad offsets"},
+        {(void **)&s.scan_flags, sizeof(int32_t) * (size_t)ntiles, "scan flags"},
+        {(void **)&s.scan_vals, sizeof(int64_t) * 6 * (size_t)ntiles, "scan values"},
+        {(void **)&s.scan_ticket, sizeof(uint32_t), "scan ticket"},
+        {(void **)&j.dtot, sizeof(sn::DevTotals), "totals"},
+    };
+    for (auto &pl : plan) {
+        sn_status r = talloc(pl.p, pl.bytes, pl.what);
+        if (r != SN_OK) return r;
+    }
+    return SN_OK;
+}
+
+// Passes 1-3 (one streaming kernel when a tile of rows fits shared memory) and
+// the scan; the totals land in j.htot once the stream reaches this point.
+sn_status job_count(ExtractJob &j, cudaStream_t st)
+{
+    if (!j.htot) {
+        j.htot = host_totals();
+        if (!j.htot) return fail(SN_ENOMEM, "pinned host allocation failed");
+    }
+    cudaError_t e = cudaMemsetAsync(j.dtot, 0, sizeof(sn::DevTotals), st);
+    if (e != cudaSuccess) return cuda_fail(e, "totals");
+    e = sn::launch_count(j.type, j.dlabels, j.cls, j.g, j.s, j.dtot, st);
+    if (e == cudaErrorNotSupported) {
+        cudaGetLastError();
+        if ((e = sn::launch_planes(j.type, j.dlabels, j.cls, j.g, j.s, st)) != cudaSuccess)
+            return cuda_fail(e, "k_planes launch");
+        e = sn::launch_cellrows(j.g, j.s, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "counting launch");
+    if ((e = sn::launch_scan(j.g, j.s, j.dtot, st)) != cudaSuccess) return cuda_fail(e, "k_scan launch");
+    e = cudaMemcpyAsync(j.htot, j.dtot, sizeof(sn::DevTotals), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "count read-back");
+    return SN_OK;
+}
+
+// Exact allocation of the outputs from the totals (end of Pass 3).
+sn_status job_allocate(ExtractJob &j, cudaStream_t st)
+{
+    const sn::DevTotals *htot = j.htot;
+    if (htot->error)
+        return fail(SN_ETIMEOUT,
+                    (htot->error & 1) ? "row scan look-back wait limit reached" : "label copy wait limit reached");
+    const int64_t np = htot->n_points, nq = htot->n_quads, ns = htot->n_stencil;
+    if (np > (int64_t)INT32_MAX) return fail(SN_EOVERFLOW, "more than INT32_MAX points");
+    sn_mesh *m = (sn_mesh *)std::calloc(1, sizeof(sn_mesh));
+    if (!m) return fail(SN_ENOMEM, "host allocation failed");
+    m->device = j.dev;
+    m->stream = st;
+    m->type = j.type;
+    m->pool = j.pool;
+    for (int a = 0; a < 3; ++a) {
+        m->dims[a] = j.dims[a];
+        m->spacing[a] = j.spacing[a];
+        m->origin[a] = j.origin[a];
+    }
+    m->np = np;
+    m->nq = nq;
+    m->ns = ns;
+    const int64_t nx = j.dims[0], ny = j.dims[1], nz = j.dims[2];
+    struct {
+        void **p;
+        size_t bytes;
+        const char *what;
+    } oplan[] = {
+        {(void **)&m->a.points, sizeof(float) * 3 * (size_t)np, "points"},
+        {(void **)&m->a.offsets, sizeof(float) * 3 * (size_t)np, "offsets"},
+        {(void **)&m->a.cells, sizeof(uint64_t) * (size_t)np, "cells"},
+        {(void **)&m->a.quads, sizeof(int32_t) * 4 * (size_t)nq, "quads"},
+        {(void **)&m->a.quad_labels, (size_t)j.type * 2 * (size_t)nq, "quad labels"},
+        {(void **)&m->a.sten_off, sizeof(int64_t) * (size_t)(np + 1), "stencil offsets"},
+        {(void **)&m->a.sten_ids, sizeof(int32_t) * (size_t)ns, "stencil ids"},
+        {(void **)&m->a.face_mask, (size_t)np, "face masks"},
+        {(void **)&m->a.meta, sizeof(int32_t) * 4, "mesh meta"},
+        {(void **)&m->a.nbr, sizeof(uint2) * (size_t)np, "smoothing neighbours"},
+        {(void **)&m->a.lut_x, sizeof(float2) * (size_t)(nx + ny + nz + 3), "cell-centre tables"},
+    };
+    for (auto &pl : oplan) {
+        sn_status r = pool_alloc(pl.p, pl.bytes, j.pool, st, pl.what);
+        if (r != SN_OK) {
+            sn_free(m);
+            return r;
+        }
+    }
+    m->a.lut_y = m->a.lut_x + (nx + 1);
+    m->a.lut_z = m->a.lut_y + (ny + 1);
+    j.mesh = m;
+    return SN_OK;
+}
+
+// Cell-centre tables and Pass 4 into the allocated mesh; emit_rows = cell rows
+// per emission tile (0: the library default).
+sn_status job_emit(ExtractJob &j, cudaStream_t st, int emit_rows)
+{
+    sn_mesh *m = j.mesh;
+    cudaError_t e = sn::launch_centre_lut(m->a, j.dims, j.spacing, j.origin, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cell-centre tables");
+    if ((e = cudaMemsetAsync(m->a.meta, 0, sizeof(int32_t) * 4, st)) != cudaSuccess) return cuda_fail(e, "mesh meta");
+    e = sn::launch_emit_tile(j.type, j.dlabels, j.cls, j.g, j.s, m->a, j.dtot, st, emit_rows);
+    if (e == cudaErrorNotSupported) {
+        cudaGetLastError();
+        e = sn::launch_emit(j.type, j.dlabels, j.cls, j.g, j.s, m->a, j.dtot, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "k_emit launch");
+    e = cudaMemcpyAsync(m->a.sten_off + m->np, j.s.offS + j.g.Rc, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "stencil offset tail");
+    return SN_OK;
+}
+
+void job_release(ExtractJob &j, cudaStream_t st)
+{
+    for (void *p : j.temps) pool_free(p, st);
+    j.temps.clear();
+    if (j.mesh) {
+        sn_free(j.mesh);
+        j.mesh = nullptr;
+    }
+    if (j.own_htot && j.htot) {
+        cudaFreeHost(j.htot);
+        j.htot = nullptr;
+    }
+}
+
+} // namespace
 
 extern "C" {
 
@@ -219,236 +500,22 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
     g_last_error.clear();
     if (!out) return fail(SN_EINVAL, "out is NULL");
     *out = nullptr;
-    if (!labels) return fail(SN_EINVAL, "labels is NULL");
-    if (type != SN_U8 && type != SN_U16 && type != SN_U32) return fail(SN_EINVAL, "bad label type");
-    if (!dims || !spacing || !origin) return fail(SN_EINVAL, "dims, spacing or origin is NULL");
-    const int64_t kMaxDim = (1ll << 21) - 2;
-    for (int a = 0; a < 3; ++a) {
-        if (dims[a] < 1 || dims[a] > kMaxDim) return fail(SN_EINVAL, "dims must be in [1, 2^21-2]");
-        if (!finite_pos(spacing[a])) return fail(SN_EINVAL, "spacing must be finite and > 0");
-        if (!std::isfinite(origin[a])) return fail(SN_EINVAL, "origin must be finite");
-    }
-    const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
-    const int64_t V = nx * ny * nz;
-    if (V >= (1ll << 40)) return fail(SN_EINVAL, "nx*ny*nz must be < 2^40");
-    const uint64_t tmax = type == SN_U8 ? 0xffull : type == SN_U16 ? 0xffffull : 0xffffffffull;
-    if ((uint64_t)background > tmax) return fail(SN_EINVAL, "background does not fit the label type");
-    if (n_selected < 0 || (n_selected > 0 && !selected) || (selected && n_selected == 0))
-        return fail(SN_EINVAL, "selected/n_selected mismatch");
-    std::vector<uint32_t> sel;
-    if (selected) {
-        sel.assign(selected, selected + n_selected);
-        for (uint32_t v : sel) {
-            if ((uint64_t)v > tmax) return fail(SN_EINVAL, "a selected label does not fit the label type");
-            if (v == background) return fail(SN_EINVAL, "a selected label equals the background value");
-        }
-        std::sort(sel.begin(), sel.end());
-        sel.erase(std::unique(sel.begin(), sel.end()), sel.end());
-    }
-
+    ExtractJob j;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    cudaMemPool_t pool;
-    e = device_pool(dev, &pool);
-    if (e != cudaSuccess) return cuda_fail(e, "memory pool");
-    sn::DevTotals *htot = host_totals();
-    if (!htot) return fail(SN_ENOMEM, "pinned host allocation failed");
-
-    std::vector<void *> temps; // freed (stream-ordered) on every exit path
-    auto cleanup = [&]() {
-        for (void *p : temps) pool_free(p, st);
-        temps.clear();
-    };
-    auto talloc = [&](void **p, size_t bytes, const char *what) -> sn_status {
-        sn_status r = pool_alloc(p, bytes, pool, st, what);
-        if (r == SN_OK) temps.push_back(*p);
-        return r;
-    };
-
-    // labels: in place when the device can read them, else one copy
-    const size_t lab_bytes = (size_t)V * (size_t)type;
-    const void *dlabels = labels;
-    cudaPointerAttributes attr;
-    e = cudaPointerGetAttributes(&attr, labels);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        attr.type = cudaMemoryTypeUnregistered;
+    sn_status r = job_prepare(j, labels, type, dims, spacing, origin, selected, n_selected, background, st);
+    if (r == SN_OK) r = job_count(j, st);
+    if (r == SN_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) r = cuda_fail(e, "count read-back");
     }
-    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
-        void *d = nullptr;
-        sn_status r = talloc(&d, lab_bytes, "label copy");
-        if (r != SN_OK) return cleanup(), r;
-        e = cudaMemcpyAsync(d, labels, lab_bytes, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return cleanup(), cuda_fail(e, "label copy");
-        dlabels = d;
+    if (r == SN_OK) r = job_allocate(j, st);
+    if (r == SN_OK) r = job_emit(j, st, 0);
+    if (r == SN_OK) {
+        *out = j.mesh;
+        j.mesh = nullptr;
     }
-
-    // classifier (Sec. 3.1)
-    sn::Classifier cls;
-    std::memset(&cls, 0, sizeof(cls));
-    cls.background = background;
-    cls.mode = sn::CLASS_ALL;
-    if (selected) {
-        const uint32_t vmax = sel.empty() ? 0u : sel.back();
-        if (vmax < (1u << 24)) {
-            cls.mode = sn::CLASS_BITMAP;
-            cls.nbits = vmax + 1u;
-            std::vector<uint32_t> bm((cls.nbits + 31) / 32, 0u);
-            for (uint32_t v : sel) bm[v >> 5] |= 1u << (v & 31u);
-            void *d = nullptr;
-            sn_status r = talloc(&d, bm.size() * 4, "label bitmap");
-            if (r != SN_OK) return cleanup(), r;
-            e = cudaMemcpyAsync(d, bm.data(), bm.size() * 4, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st); // bm is a local vector
-            if (e != cudaSuccess) return cleanup(), cuda_fail(e, "label bitmap copy");
-            cls.bitmap = (const uint32_t *)d;
-        } else {
-            cls.mode = sn::CLASS_SORTED;
-            cls.nsorted = (int64_t)sel.size();
-            void *d = nullptr;
-            sn_status r = talloc(&d, sel.size() * 4, "label list");
-            if (r != SN_OK) return cleanup(), r;
-            e = cudaMemcpyAsync(d, sel.data(), sel.size() * 4, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return cleanup(), cuda_fail(e, "label list copy");
-            cls.sorted = (const uint32_t *)d;
-        }
-    }
-
-    sn::Geometry g;
-    g.nx = nx;
-    g.ny = ny;
-    g.nz = nz;
-    g.W = (nx + 1 + 31) / 32;
-    g.WS = (g.W + 3) / 4 * 4;
-    g.Rs = ny * nz;
-    g.Rc = (ny + 1) * (nz + 1);
-    g.lp = nx;
-    const int ntiles = (int)((g.Rc + sn::kScanTile - 1) / sn::kScanTile);
-
-    sn::ExtractScratch s;
-    std::memset(&s, 0, sizeof(s));
-    struct {
-        void **p;
-        size_t bytes;
-        const char *what;
-    } plan[] = {
-        {(void **)&s.X, sizeof(uint32_t) * (size_t)(g.Rs * g.WS), "X plane"},
-        {(void **)&s.Y, sizeof(uint32_t) * (size_t)(g.Rs * g.WS), "Y plane"},
-        {(void **)&s.Z, sizeof(uint32_t) * (size_t)(g.Rs * g.WS), "Z plane"},
-        {(void **)&s.P, sizeof(uint32_t) * (size_t)(g.Rc * g.WS), "point plane"},
-        {(void **)&s.cntP, sizeof(int32_t) * (size_t)g.Rc, "point counts"},
-        {(void **)&s.cntS, sizeof(int32_t) * (size_t)g.Rc, "stencil counts"},
-        {(void **)&s.cntQ, sizeof(int32_t) * (size_t)g.Rc, "quad counts"},
-        {(void **)&s.offP, sizeof(int64_t) * (size_t)(g.Rc + 1), "point offsets"},
-        {(void **)&s.offS, sizeof(int64_t) * (size_t)(g.Rc + 1), "stencil offsets"},
-        {(void **)&s.offQ, sizeof(int64_t) * (size_t)(g.Rc + 1), "quad offsets"},
-        {(void **)&s.scan_flags, sizeof(int32_t) * (size_t)ntiles, "scan flags"},
-        {(void **)&s.scan_vals, sizeof(int64_t) * 6 * (size_t)ntiles, "scan values"},
-        {(void **)&s.scan_ticket, sizeof(uint32_t), "scan ticket"},
-    };
-    for (auto &pl : plan) {
-        sn_status r = talloc(pl.p, pl.bytes, pl.what);
-        if (r != SN_OK) return cleanup(), r;
-    }
-    sn::DevTotals *dtot = nullptr;
-    {
-        sn_status r = talloc((void **)&dtot, sizeof(sn::DevTotals), "totals");
-        if (r != SN_OK) return cleanup(), r;
-    }
-
-    // Passes 1-3: one streaming kernel when a tile of rows fits shared memory
-    if ((e = cudaMemsetAsync(dtot, 0, sizeof(sn::DevTotals), st)) != cudaSuccess)
-        return cleanup(), cuda_fail(e, "totals");
-    e = sn::launch_count(type, dlabels, cls, g, s, dtot, st);
-    if (e == cudaErrorNotSupported) {
-        cudaGetLastError();
-        if ((e = sn::launch_planes(type, dlabels, cls, g, s, st)) != cudaSuccess)
-            return cleanup(), cuda_fail(e, "k_planes launch");
-        e = sn::launch_cellrows(g, s, st);
-    }
-    if (e != cudaSuccess) return cleanup(), cuda_fail(e, "counting launch");
-    if ((e = sn::launch_scan(g, s, dtot, st)) != cudaSuccess) return cleanup(), cuda_fail(e, "k_scan launch");
-    e = cudaMemcpyAsync(htot, dtot, sizeof(sn::DevTotals), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cleanup(), cuda_fail(e, "count read-back");
-    if (htot->error)
-        return cleanup(), fail(SN_ETIMEOUT, (htot->error & 1) ? "row scan look-back wait limit reached"
-                                                              : "label copy wait limit reached");
-    const int64_t np = htot->n_points, nq = htot->n_quads, ns = htot->n_stencil;
-    if (np > (int64_t)INT32_MAX) return cleanup(), fail(SN_EOVERFLOW, "more than INT32_MAX points");
-
-    // exact allocation of the outputs (end of Pass 3)
-    sn_mesh *m = (sn_mesh *)std::calloc(1, sizeof(sn_mesh));
-    if (!m) return cleanup(), fail(SN_ENOMEM, "host allocation failed");
-    m->device = dev;
-    m->stream = st;
-    m->type = type;
-    m->pool = pool;
-    for (int a = 0; a < 3; ++a) {
-        m->dims[a] = dims[a];
-        m->spacing[a] = spacing[a];
-        m->origin[a] = origin[a];
-    }
-    m->np = np;
-    m->nq = nq;
-    m->ns = ns;
-    struct {
-        void **p;
-        size_t bytes;
-        const char *what;
-    } oplan[] = {
-        {(void **)&m->a.points, sizeof(float) * 3 * (size_t)np, "points"},
-        {(void **)&m->a.offsets, sizeof(float) * 3 * (size_t)np, "offsets"},
-        {(void **)&m->a.cells, sizeof(uint64_t) * (size_t)np, "cells"},
-        {(void **)&m->a.quads, sizeof(int32_t) * 4 * (size_t)nq, "quads"},
-        {(void **)&m->a.quad_labels, (size_t)type * 2 * (size_t)nq, "quad labels"},
-        {(void **)&m->a.sten_off, sizeof(int64_t) * (size_t)(np + 1), "stencil offsets"},
-        {(void **)&m->a.sten_ids, sizeof(int32_t) * (size_t)ns, "stencil ids"},
-        {(void **)&m->a.face_mask, (size_t)np, "face masks"},
-        {(void **)&m->a.meta, sizeof(int32_t) * 4, "mesh meta"},
-        {(void **)&m->a.nbr, sizeof(uint2) * (size_t)np, "smoothing neighbours"},
-        {(void **)&m->a.lut_x, sizeof(float2) * (size_t)(nx + ny + nz + 3), "cell-centre tables"},
-    };
-    for (auto &pl : oplan) {
-        sn_status r = pool_alloc(pl.p, pl.bytes, pool, st, pl.what);
-        if (r != SN_OK) {
-            sn_free(m);
-            return cleanup(), r;
-        }
-    }
-
-    m->a.lut_y = m->a.lut_x + (nx + 1);
-    m->a.lut_z = m->a.lut_y + (ny + 1);
-    if ((e = sn::launch_centre_lut(m->a, dims, spacing, origin, st)) != cudaSuccess) {
-        sn_free(m);
-        return cleanup(), cuda_fail(e, "cell-centre tables");
-    }
-
-    // Pass 4
-    if ((e = cudaMemsetAsync(m->a.meta, 0, sizeof(int32_t) * 4, st)) != cudaSuccess) {
-        sn_free(m);
-        return cleanup(), cuda_fail(e, "mesh meta");
-    }
-    e = sn::launch_emit_tile(type, dlabels, cls, g, s, m->a, dtot, st);
-    if (e == cudaErrorNotSupported) {
-        cudaGetLastError();
-        e = sn::launch_emit(type, dlabels, cls, g, s, m->a, dtot, st);
-    }
-    if (e != cudaSuccess) {
-        sn_free(m);
-        return cleanup(), cuda_fail(e, "k_emit launch");
-    }
-    e = cudaMemcpyAsync(m->a.sten_off + np, s.offS + g.Rc, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) {
-        sn_free(m);
-        return cleanup(), cuda_fail(e, "stencil offset tail");
-    }
-    cleanup();
-    *out = m;
-    return SN_OK;
+    job_release(j, st);
+    return r;
 }
 
 sn_status sn_smooth(sn_mesh *m, int iterations, float relaxation, float constraint_distance)
@@ -862,6 +929,264 @@ sn_status sn_smooth_learned(sn_mesh *m, const sn_learner *l, int corrections, fl
                                    start == m->a.offsets ? m->smooth_scratch : m->a.offsets, m->spacing, m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "learned smoothing launch");
     return SN_OK;
+}
+
+} // extern "C"
+
+// ------------------------------------------------------------ batched maps
+namespace {
+
+constexpr int kBatchStreams = 8;
+
+// pinned totals of a batch, one per map; per thread, grown as needed and kept
+sn::DevTotals *batch_totals(int64_t n)
+{
+    thread_local sn::DevTotals *buf = nullptr;
+    thread_local int64_t cap = 0;
+    if (n > cap) {
+        if (buf) cudaFreeHost(buf);
+        buf = nullptr;
+        cap = 0;
+        int64_t c = 256;
+        while (c < n) c *= 2;
+        if (cudaMallocHost((void **)&buf, sizeof(sn::DevTotals) * (size_t)c) != cudaSuccess) {
+            cudaGetLastError();
+            buf = nullptr;
+            return nullptr;
+        }
+        cap = c;
+    }
+    return buf;
+}
+
+// kBatchStreams side streams and one capture-origin stream of this thread on
+// the current device (created once, kept; non-blocking, so capturable)
+cudaError_t side_streams(int dev, cudaStream_t *out)
+{
+    thread_local std::map<int, std::vector<cudaStream_t>> cache;
+    auto &v = cache[dev];
+    if (v.empty()) {
+        for (int i = 0; i <= kBatchStreams; ++i) {
+            cudaStream_t s = nullptr;
+            cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+            if (e != cudaSuccess) {
+                for (cudaStream_t t : v) cudaStreamDestroy(t);
+                v.clear();
+                return e;
+            }
+            v.push_back(s);
+        }
+    }
+    for (int i = 0; i <= kBatchStreams; ++i) out[i] = v[i];
+    return cudaSuccess;
+}
+
+// Tile height of the emission per (label type, words per row, cell rows, cell
+// slices) bucket, chosen by timing the candidates on the first map of the bucket.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int64_t, int64_t, int64_t>, int> g_tune;
+const int kTuneRows[] = {8, 16, 24, 32};
+
+std::tuple<int, int64_t, int64_t, int64_t> tune_key(const ExtractJob &j)
+{
+    auto bucket = [](int64_t v) { return v <= 64 ? 64 : v <= 128 ? 128 : v <= 256 ? 256 : 512; };
+    return std::make_tuple((int)j.type, j.g.W, bucket(j.g.ny + 1), bucket(j.g.nz + 1));
+}
+
+sn_status tune_emit_rows(ExtractJob &j, cudaStream_t st, int *rows)
+{
+    const auto key = tune_key(j);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            *rows = it->second;
+            return SN_OK;
+        }
+    }
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    int best = 0;
+    float best_ms = 0.f;
+    for (int r : kTuneRows) {
+        if (e != cudaSuccess) break;
+        sn_status st1 = job_emit(j, st, r); // warm-up and check
+        if (st1 != SN_OK) {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+            return st1;
+        }
+        e = cudaEventRecord(a, st);
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+            if (job_emit(j, st, r) != SN_OK) e = cudaErrorUnknown;
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && (best == 0 || ms < best_ms)) {
+            best = r;
+            best_ms = ms;
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_fail(e, "emission tuning");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+    *rows = best;
+    return SN_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, const sn_label_type *types,
+                                  const int64_t *dims, const double *spacing, const double *origin,
+                                  uint32_t background, int iterations, float relaxation, float constraint_distance,
+                                  int flags, void *cuda_stream, sn_mesh **out)
+{
+    g_last_error.clear();
+    if (n_maps < 0 || (n_maps > 0 && (!labels || !types || !dims || !out)))
+        return fail(SN_EINVAL, "n_maps < 0 or a NULL array");
+    if (iterations < 0) return fail(SN_EINVAL, "iterations must be >= 0");
+    if (!std::isfinite(relaxation) || relaxation < 0.f) return fail(SN_EINVAL, "relaxation must be finite and >= 0");
+    if (!std::isfinite(constraint_distance) || constraint_distance < 0.f)
+        return fail(SN_EINVAL, "constraint distance must be finite and >= 0");
+    if (flags & ~(SN_BATCH_GRAPH | SN_BATCH_TUNE)) return fail(SN_EINVAL, "unknown flags");
+    for (int64_t i = 0; i < n_maps; ++i) out[i] = nullptr;
+    if (n_maps == 0) return SN_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    cudaStream_t side[kBatchStreams + 1];
+    if ((e = side_streams(dev, side)) != cudaSuccess) return cuda_fail(e, "side streams");
+    cudaStream_t cap = side[kBatchStreams]; // origin of the capture (the caller's stream may be the legacy one)
+
+    std::vector<ExtractJob> jobs((size_t)n_maps);
+    sn::DevTotals *htot = nullptr;
+    std::vector<cudaEvent_t> events;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool capturing = false;
+    auto finish = [&](sn_status r) {
+        if (capturing) {
+            cudaGraph_t g2 = nullptr;
+            cudaStreamEndCapture(cap, &g2);
+            if (g2) cudaGraphDestroy(g2);
+            cudaGetLastError();
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (r != SN_OK) { // work of this call may still be running on the side streams
+            for (int k = 0; k <= kBatchStreams; ++k) cudaStreamSynchronize(side[k]);
+            cudaStreamSynchronize(st);
+            cudaGetLastError();
+        }
+        for (auto &j : jobs) {
+            if (r == SN_OK) j.mesh = nullptr; // handed out
+            job_release(j, st);
+        }
+        for (cudaEvent_t ev : events) cudaEventDestroy(ev);
+        return r;
+    };
+    auto event = [&](cudaEvent_t *ev) -> cudaError_t {
+        cudaError_t e2 = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e2 == cudaSuccess) events.push_back(*ev);
+        return e2;
+    };
+    const double one[3] = {1.0, 1.0, 1.0}, zero[3] = {0.0, 0.0, 0.0};
+
+    // 1. checks, label copies, scratch (main stream)
+    for (int64_t i = 0; i < n_maps; ++i) {
+        sn_status r = job_prepare(jobs[i], labels[i], types[i], dims + 3 * i, spacing ? spacing + 3 * i : one,
+                                  origin ? origin + 3 * i : zero, nullptr, 0, background, st);
+        if (r != SN_OK) return finish(r);
+    }
+    if (!(htot = batch_totals(n_maps))) return finish(fail(SN_ENOMEM, "pinned totals"));
+    for (int64_t i = 0; i < n_maps; ++i) jobs[i].htot = htot + i;
+
+    // 2. Passes 1-3 and the scans of all maps on the side streams, then one wait
+    cudaEvent_t fork = nullptr;
+    if ((e = event(&fork)) != cudaSuccess || (e = cudaEventRecord(fork, st)) != cudaSuccess)
+        return finish(cuda_fail(e, "batch fork"));
+    for (int k = 0; k < kBatchStreams; ++k)
+        if ((e = cudaStreamWaitEvent(side[k], fork, 0)) != cudaSuccess) return finish(cuda_fail(e, "batch fork"));
+    for (int64_t i = 0; i < n_maps; ++i) {
+        sn_status r = job_count(jobs[i], side[i % kBatchStreams]);
+        if (r != SN_OK) return finish(r);
+    }
+    for (int k = 0; k < kBatchStreams; ++k) {
+        cudaEvent_t join = nullptr;
+        if ((e = event(&join)) != cudaSuccess || (e = cudaEventRecord(join, side[k])) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess)
+            return finish(cuda_fail(e, "batch join"));
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return finish(cuda_fail(e, "count read-back"));
+
+    // 3. exact outputs and smoothing buffers (main stream); tile heights
+    std::vector<int> rows((size_t)n_maps, 0);
+    for (int64_t i = 0; i < n_maps; ++i) {
+        sn_status r = job_allocate(jobs[i], st);
+        if (r != SN_OK) return finish(r);
+        sn_mesh *m = jobs[i].mesh;
+        if (iterations > 0 && m->np > 0) {
+            r = pool_alloc((void **)&m->smooth_scratch, sizeof(float) * 3 * (size_t)m->np, m->pool, st,
+                           "smoothing buffer");
+            if (r != SN_OK) return finish(r);
+        }
+        if (flags & SN_BATCH_TUNE) {
+            r = tune_emit_rows(jobs[i], st, &rows[i]);
+            if (r != SN_OK) return finish(r);
+        }
+    }
+
+    // 4. Pass 4 and the smoothing of every map on the side streams, captured
+    //    into one graph (maps on parallel branches, launched once on the
+    //    caller's stream) or launched directly
+    const bool use_graph = (flags & SN_BATCH_GRAPH) != 0;
+    cudaStream_t origin_st = use_graph ? cap : st;
+    if (use_graph) {
+        if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+            return finish(cuda_fail(e, "graph capture begin"));
+        capturing = true;
+    }
+    cudaEvent_t fork2 = nullptr;
+    if ((e = event(&fork2)) != cudaSuccess || (e = cudaEventRecord(fork2, origin_st)) != cudaSuccess)
+        return finish(cuda_fail(e, "batch fork"));
+    for (int k = 0; k < kBatchStreams; ++k)
+        if ((e = cudaStreamWaitEvent(side[k], fork2, 0)) != cudaSuccess) return finish(cuda_fail(e, "batch fork"));
+    const float half = 0.5f * constraint_distance;
+    for (int64_t i = 0; i < n_maps; ++i) {
+        cudaStream_t ss = side[i % kBatchStreams];
+        sn_status r = job_emit(jobs[i], ss, rows[i]);
+        if (r != SN_OK) return finish(r);
+        sn_mesh *m = jobs[i].mesh;
+        if (iterations > 0 && m->np > 0) {
+            e = sn::launch_smooth(m->a, m->np, iterations, relaxation, half, 0, m->smooth_scratch, m->spacing, ss);
+            if (e != cudaSuccess) return finish(cuda_fail(e, "smoothing launch"));
+        }
+    }
+    for (int k = 0; k < kBatchStreams; ++k) {
+        cudaEvent_t join = nullptr;
+        if ((e = event(&join)) != cudaSuccess || (e = cudaEventRecord(join, side[k])) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(origin_st, join, 0)) != cudaSuccess)
+            return finish(cuda_fail(e, "batch join"));
+    }
+    if (use_graph) {
+        capturing = false;
+        if ((e = cudaStreamEndCapture(cap, &graph)) != cudaSuccess) return finish(cuda_fail(e, "graph capture end"));
+        if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
+            return finish(cuda_fail(e, "graph instantiate"));
+        if ((e = cudaGraphLaunch(exec, st)) != cudaSuccess) return finish(cuda_fail(e, "graph launch"));
+    }
+    for (int64_t i = 0; i < n_maps; ++i) {
+        jobs[i].mesh->stream = st;
+        out[i] = jobs[i].mesh;
+    }
+    return finish(SN_OK);
 }
 
 } // extern "C"

@@ -34,7 +34,11 @@ template <typename T, int MODE>
 cudaError_t emit_tile_t(const void *labels, const Classifier &c, const Geometry &g, const ExtractScratch &s,
                         const MeshArrays &m, DevTotals *tot, const TileGeom &tg, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_emit_tile<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // one fixed limit (the largest tile any launch may use), so that launches captured
+    // into one graph with different tile shapes all stay within it
+    static const int kMaxSmem = (int)(sizeof(uint32_t) * (size_t)TileSmem(kEmitMaxRows, kTileMaxW, kTileMaxW).total);
+    if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_emit_tile<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((g.ny + 1 + tg.ty - 1) / tg.ty), (unsigned)(g.nz + 1));
     k_emit_tile<T, MODE><<<grid, 256, smem, st>>>((const T *)labels, c, g, s, m, tot, tg);
@@ -54,11 +58,12 @@ cudaError_t emit_tile_m(int type, const void *labels, const Classifier &c, const
 } // namespace
 
 cudaError_t launch_emit_tile(int type, const void *labels, const Classifier &c, const Geometry &g,
-                             const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st)
+                             const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st, int rows)
 {
     if (g.W > kTileMaxW || g.nz + 1 > 65535) return cudaErrorNotSupported;
+    if (rows < 0 || rows > kEmitMaxRows) return cudaErrorInvalidValue;
     TileGeom tg;
-    tg.ty = kTileRows;
+    tg.ty = rows ? rows : kTileRows;
     tg.W = (int)g.W;
     tg.WS = (int)g.WS;
     tg.ns = 3 * (tg.ty + 2);

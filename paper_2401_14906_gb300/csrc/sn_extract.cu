@@ -417,12 +417,17 @@ cudaError_t emit_m(int type, const void *labels, const Classifier &c, const Geom
 }
 
 
+constexpr size_t kCountMaxSmem = 200 * 1024;
+
 template <typename T, int MODE, bool FAST>
 cudaError_t count_f(const void *labels, const Classifier &c, const Geometry &g, const ExtractScratch &s,
                     const CountTiling &tl, size_t smem, DevTotals *tot, cudaStream_t st)
 {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_count<T, MODE, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // one fixed limit for every launch (launch_count rejects tiles above it), so that
+    // launches captured into one graph with different tilings all stay within it
+    if (smem > kCountMaxSmem) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_count<T, MODE, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kCountMaxSmem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((g.ny + tl.ty - 1) / tl.ty), (unsigned)((g.nz + tl.kz - 1) / tl.kz));
     k_count<T, MODE, FAST><<<grid, 256, smem, st>>>((const T *)labels, c, g, s, tl, tot);
@@ -521,7 +526,7 @@ cudaError_t launch_count(int type, const void *labels, const Classifier &c, cons
     tl.kz = (int)kz;
     // + 256: the packed compares read up to 33 samples past a row's last word
     const size_t smem = kCountHeader + (size_t)kCountSlots * tl.slot_bytes + 2 * 3 * (size_t)(ty + 1) * g.W * 4 + 256;
-    if (smem > 200 * 1024) return cudaErrorNotSupported;
+    if (smem > kCountMaxSmem) return cudaErrorNotSupported;
     cudaError_t e = cudaMemsetAsync(s.cntQ, 0, sizeof(int32_t) * (size_t)g.Rc, st);
     if (e != cudaSuccess) return e;
     ProfScope ps("k_count", st);

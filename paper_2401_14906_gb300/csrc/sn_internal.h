@@ -99,6 +99,7 @@ struct TileGeom {
     uint64_t wdiv; // ceil(2^32 / W): it / W == (it * wdiv) >> 32
 };
 
+constexpr int kEmitMaxRows = 32;
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
@@ -117,9 +118,11 @@ cudaError_t launch_emit(int type, const void *labels, const Classifier &c, const
                         const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st);
 
 // Pass 4 over tiles of cell rows (sn_emit.cu); cudaErrorNotSupported for rows too
-// wide for its shared-memory staging (launch_emit is used then).
+// wide for its shared-memory staging (launch_emit is used then).  rows = cell
+// rows per tile, 1..kEmitMaxRows (0: the default).
 cudaError_t launch_emit_tile(int type, const void *labels, const Classifier &c, const Geometry &g,
-                             const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st);
+                             const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st,
+                             int rows = 0);
 
 // per-axis cell-centre tables of a mesh (sn_extract.cu)
 cudaError_t launch_centre_lut(const MeshArrays &m, const int64_t dims[3], const double spacing[3],

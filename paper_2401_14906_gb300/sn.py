@@ -54,6 +54,9 @@ SIGNATURES = {
     "sn_last_error": (ctypes.c_char_p, []),
     "sn_smooth_static": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                         _P, _P]),
+    "sn_extract_smooth_batch": (ctypes.c_int, [ctypes.c_int64, _P, _P, _I64P, _DP, _DP, ctypes.c_uint32,
+                                               ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_int, _P,
+                                               ctypes.POINTER(_P)]),
     "sn_learner_create": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
     "sn_learner_free": (None, [_P]),
     "sn_learner_set_params": (ctypes.c_int, [_P, _P]),
@@ -308,6 +311,42 @@ def sn_profile_read(reset=False):
     buf = (sn_kernel_time * 64)()
     n = lib.sn_profile_read(buf, 64, 1 if reset else 0)
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n, 64))}
+
+
+# ------------------------------------------------------------ batched maps
+SN_BATCH_GRAPH, SN_BATCH_TUNE = 1, 2
+
+
+def sn_extract_smooth_batch(maps, spacing=None, origin=None, background=0, iterations=16, relaxation=0.5,
+                            constraint_distance=1.0, graph=True, tune=True, stream=None):
+    """Extract and smooth a list of (nz, ny, nx) label maps (device tensors or host arrays) in one call.
+
+    Returns a list of Mesh objects, one per map."""
+    lib = load()
+    n = len(maps)
+    infos = [_label_info(m) for m in maps]
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[ctypes.c_void_p(i[0]) for i in infos])
+    types = (ctypes.c_int * max(n, 1))(*[i[1] for i in infos])
+    dims = (ctypes.c_int64 * max(3 * n, 1))(*[d for i in infos for d in i[2]])
+    sp = org = None
+    if spacing is not None:
+        sp = (ctypes.c_double * (3 * n))(*[float(v) for s3 in spacing for v in s3])
+    if origin is not None:
+        org = (ctypes.c_double * (3 * n))(*[float(v) for o3 in origin for v in o3])
+    out = (ctypes.c_void_p * max(n, 1))()
+    flags = (SN_BATCH_GRAPH if graph else 0) | (SN_BATCH_TUNE if tune else 0)
+    is_cuda = any(i[3] for i in infos)
+    rc = lib.sn_extract_smooth_batch(n, ctypes.cast(ptrs, ctypes.c_void_p), ctypes.cast(types, ctypes.c_void_p),
+                                     dims, sp, org, int(background), int(iterations), float(relaxation),
+                                     float(constraint_distance), flags,
+                                     ctypes.c_void_p(_stream_handle(stream, is_cuda or True)), out)
+    keep = infos  # noqa: F841 -- the label buffers must live until the call has enqueued its work
+    _check(rc)
+    res = []
+    for k in range(n):
+        res.append(Mesh(out[k], infos[k][1], infos[k][2], spacing[k] if spacing is not None else (1.0, 1.0, 1.0),
+                        origin[k] if origin is not None else (0.0, 0.0, 0.0)))
+    return res
 
 
 # ------------------------------------------------------- learned proposal
