@@ -501,8 +501,8 @@ def run_batch(args):
     labs = [to_device(w.labels) for w in ws]
     it, lam, d = ws[0].iterations, ws[0].relaxation, ws[0].constraint
 
-    def batched():
-        ms = sn.sn_extract_smooth_batch(labs, iterations=it, relaxation=lam, constraint_distance=d)
+    def batched(graph=False):
+        ms = sn.sn_extract_smooth_batch(labs, iterations=it, relaxation=lam, constraint_distance=d, graph=graph)
         torch.cuda.synchronize()
         return ms
 
@@ -532,6 +532,7 @@ def run_batch(args):
     time.sleep(0.3)
     ms_batch = timed(batched)
     clocks = sampler.stop()
+    ms_graph = timed(lambda: batched(True))
     ms_loop = timed(looped)
     counts = [m.counts for m in batched()]
     P = sum(c[0] for c in counts)
@@ -540,7 +541,10 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "u8/u16+f32", "data": "synthetic",
             "config": {"workload": "c5_256maps_edges32-256_u8u16", "maps": len(ws), "voxels": V, "points": P,
                        "iterations": it, "timing": "host clock around each step (allocation, launches, waits)",
-                       "batched": "sn_extract_smooth_batch: 8 streams, one CUDA graph, tuned emission tiles",
+                       "batched": "sn_extract_smooth_batch: counting on 8 streams, one totals wait, emission on 8 "
+                                  "streams, one sweep launch per iteration over all maps, tuned emission tiles",
+                       "graph_mode_ms_per_step": ms_graph,
+                       "graph_mode_gvoxels_s": V / (ms_graph / 1e3) / 1e9,
                        "single_map_loop_ms_per_step": ms_loop,
                        "single_map_loop_gvoxels_s": V / (ms_loop / 1e3) / 1e9},
             "clocks": clocks}

@@ -27,6 +27,8 @@ struct sn_mesh {
     float *smooth_scratch;
     int32_t *tris;
     cudaMemPool_t pool;
+    char *arena;        // one block holding the output arrays (and the batch's smoothing buffer)
+    size_t arena_bytes;
 };
 
 struct sn_learner {
@@ -322,23 +324,32 @@ sn_status job_prepare(ExtractJob &j, const void *labels, sn_label_type type, con
         {(void **)&s.scan_ticket, sizeof(uint32_t), "scan ticket"},
         {(void **)&j.dtot, sizeof(sn::DevTotals), "totals"},
     };
+    // one block for all of them, each array on a 256-byte boundary
+    size_t total = 0;
+    for (auto &pl : plan) total += (pl.bytes + 255) / 256 * 256;
+    char *block = nullptr;
+    sn_status r = talloc((void **)&block, total, "extraction scratch");
+    if (r != SN_OK) return r;
     for (auto &pl : plan) {
-        sn_status r = talloc(pl.p, pl.bytes, pl.what);
-        if (r != SN_OK) return r;
+        *pl.p = block;
+        block += (pl.bytes + 255) / 256 * 256;
     }
     return SN_OK;
 }
 
 // Passes 1-3 (one streaming kernel when a tile of rows fits shared memory) and
 // the scan; the totals land in j.htot once the stream reaches this point.
-sn_status job_count(ExtractJob &j, cudaStream_t st)
+sn_status job_count(ExtractJob &j, cudaStream_t st, bool shared_totals = false)
 {
-    if (!j.htot) {
-        j.htot = host_totals();
-        if (!j.htot) return fail(SN_ENOMEM, "pinned host allocation failed");
+    cudaError_t e = cudaSuccess;
+    if (!shared_totals) { // else the caller clears and reads back the totals of many jobs at once
+        if (!j.htot) {
+            j.htot = host_totals();
+            if (!j.htot) return fail(SN_ENOMEM, "pinned host allocation failed");
+        }
+        e = cudaMemsetAsync(j.dtot, 0, sizeof(sn::DevTotals), st);
+        if (e != cudaSuccess) return cuda_fail(e, "totals");
     }
-    cudaError_t e = cudaMemsetAsync(j.dtot, 0, sizeof(sn::DevTotals), st);
-    if (e != cudaSuccess) return cuda_fail(e, "totals");
     e = sn::launch_count(j.type, j.dlabels, j.cls, j.g, j.s, j.dtot, st);
     if (e == cudaErrorNotSupported) {
         cudaGetLastError();
@@ -348,13 +359,16 @@ sn_status job_count(ExtractJob &j, cudaStream_t st)
     }
     if (e != cudaSuccess) return cuda_fail(e, "counting launch");
     if ((e = sn::launch_scan(j.g, j.s, j.dtot, st)) != cudaSuccess) return cuda_fail(e, "k_scan launch");
-    e = cudaMemcpyAsync(j.htot, j.dtot, sizeof(sn::DevTotals), cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return cuda_fail(e, "count read-back");
+    if (!shared_totals) {
+        e = cudaMemcpyAsync(j.htot, j.dtot, sizeof(sn::DevTotals), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "count read-back");
+    }
     return SN_OK;
 }
 
-// Exact allocation of the outputs from the totals (end of Pass 3).
-sn_status job_allocate(ExtractJob &j, cudaStream_t st)
+// Exact allocation of the outputs from the totals (end of Pass 3), in one
+// block; with_smooth_buffer also places the smoothing buffer there.
+sn_status job_allocate(ExtractJob &j, cudaStream_t st, bool with_smooth_buffer = false)
 {
     const sn::DevTotals *htot = j.htot;
     if (htot->error)
@@ -394,13 +408,22 @@ sn_status job_allocate(ExtractJob &j, cudaStream_t st)
         {(void **)&m->a.nbr, sizeof(uint2) * (size_t)np, "smoothing neighbours"},
         {(void **)&m->a.lut_x, sizeof(float2) * (size_t)(nx + ny + nz + 3), "cell-centre tables"},
     };
-    for (auto &pl : oplan) {
-        sn_status r = pool_alloc(pl.p, pl.bytes, j.pool, st, pl.what);
-        if (r != SN_OK) {
-            sn_free(m);
-            return r;
-        }
+    // one block for all outputs (+ the smoothing buffer when asked), each array on a 256-byte boundary
+    const size_t smooth_bytes = with_smooth_buffer ? sizeof(float) * 3 * (size_t)np : 0;
+    size_t total = (smooth_bytes + 255) / 256 * 256;
+    for (auto &pl : oplan) total += (pl.bytes + 255) / 256 * 256;
+    sn_status r = pool_alloc((void **)&m->arena, total, j.pool, st, "mesh outputs");
+    if (r != SN_OK) {
+        sn_free(m);
+        return r;
     }
+    m->arena_bytes = total;
+    char *block = m->arena;
+    for (auto &pl : oplan) {
+        *pl.p = block;
+        block += (pl.bytes + 255) / 256 * 256;
+    }
+    if (smooth_bytes) m->smooth_scratch = reinterpret_cast<float *>(block);
     m->a.lut_y = m->a.lut_x + (nx + 1);
     m->a.lut_z = m->a.lut_y + (ny + 1);
     j.mesh = m;
@@ -409,20 +432,27 @@ sn_status job_allocate(ExtractJob &j, cudaStream_t st)
 
 // Cell-centre tables and Pass 4 into the allocated mesh; emit_rows = cell rows
 // per emission tile (0: the library default).
-sn_status job_emit(ExtractJob &j, cudaStream_t st, int emit_rows)
+sn_status job_emit(ExtractJob &j, cudaStream_t st, int emit_rows, bool batched = false)
 {
     sn_mesh *m = j.mesh;
-    cudaError_t e = sn::launch_centre_lut(m->a, j.dims, j.spacing, j.origin, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cell-centre tables");
-    if ((e = cudaMemsetAsync(m->a.meta, 0, sizeof(int32_t) * 4, st)) != cudaSuccess) return cuda_fail(e, "mesh meta");
+    cudaError_t e = cudaSuccess;
+    if (!batched) { // else one launch prepares the tables and meta words of many meshes
+        e = sn::launch_centre_lut(m->a, j.dims, j.spacing, j.origin, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cell-centre tables");
+        if ((e = cudaMemsetAsync(m->a.meta, 0, sizeof(int32_t) * 4, st)) != cudaSuccess)
+            return cuda_fail(e, "mesh meta");
+    }
     e = sn::launch_emit_tile(j.type, j.dlabels, j.cls, j.g, j.s, m->a, j.dtot, st, emit_rows);
     if (e == cudaErrorNotSupported) {
         cudaGetLastError();
         e = sn::launch_emit(j.type, j.dlabels, j.cls, j.g, j.s, m->a, j.dtot, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "k_emit launch");
-    e = cudaMemcpyAsync(m->a.sten_off + m->np, j.s.offS + j.g.Rc, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "stencil offset tail");
+    if (!batched) {
+        e = cudaMemcpyAsync(m->a.sten_off + m->np, j.s.offS + j.g.Rc, sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                            st);
+        if (e != cudaSuccess) return cuda_fail(e, "stencil offset tail");
+    }
     return SN_OK;
 }
 
@@ -640,7 +670,12 @@ void sn_free(sn_mesh *m)
     void *ps[] = {m->a.points,    m->a.offsets, m->a.cells, m->a.quads, m->a.quad_labels, m->a.sten_off,
                   m->a.sten_ids,  m->a.face_mask, m->a.meta,  m->a.nbr,   m->a.lut_x,       m->smooth_scratch,
                   m->tris};
-    for (void *p : ps) pool_free(p, m->stream);
+    for (void *p : ps) {
+        const char *c = static_cast<const char *>(p);
+        if (m->arena && c >= m->arena && c < m->arena + m->arena_bytes) continue; // part of the arena
+        pool_free(p, m->stream);
+    }
+    pool_free(m->arena, m->stream);
     std::free(m);
 }
 
@@ -1106,7 +1141,20 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
         if (r != SN_OK) return finish(r);
     }
     if (!(htot = batch_totals(n_maps))) return finish(fail(SN_ENOMEM, "pinned totals"));
-    for (int64_t i = 0; i < n_maps; ++i) jobs[i].htot = htot + i;
+    // the device totals of all maps in one array: one clear, one read-back
+    sn::DevTotals *dtot_all = nullptr;
+    {
+        sn_status r = pool_alloc((void **)&dtot_all, sizeof(sn::DevTotals) * (size_t)n_maps, jobs[0].pool, st,
+                                 "batch totals");
+        if (r != SN_OK) return finish(r);
+        jobs[0].temps.push_back(dtot_all);
+        if ((e = cudaMemsetAsync(dtot_all, 0, sizeof(sn::DevTotals) * (size_t)n_maps, st)) != cudaSuccess)
+            return finish(cuda_fail(e, "batch totals"));
+    }
+    for (int64_t i = 0; i < n_maps; ++i) {
+        jobs[i].htot = htot + i;
+        jobs[i].dtot = dtot_all + i;
+    }
 
     // 2. Passes 1-3 and the scans of all maps on the side streams, then one wait
     cudaEvent_t fork = nullptr;
@@ -1115,7 +1163,7 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
     for (int k = 0; k < kBatchStreams; ++k)
         if ((e = cudaStreamWaitEvent(side[k], fork, 0)) != cudaSuccess) return finish(cuda_fail(e, "batch fork"));
     for (int64_t i = 0; i < n_maps; ++i) {
-        sn_status r = job_count(jobs[i], side[i % kBatchStreams]);
+        sn_status r = job_count(jobs[i], side[i % kBatchStreams], true);
         if (r != SN_OK) return finish(r);
     }
     for (int k = 0; k < kBatchStreams; ++k) {
@@ -1124,23 +1172,90 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
             (e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess)
             return finish(cuda_fail(e, "batch join"));
     }
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return finish(cuda_fail(e, "count read-back"));
+    e = cudaMemcpyAsync(htot, dtot_all, sizeof(sn::DevTotals) * (size_t)n_maps, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return finish(cuda_fail(e, "count read-back"));
 
     // 3. exact outputs and smoothing buffers (main stream); tile heights
     std::vector<int> rows((size_t)n_maps, 0);
     for (int64_t i = 0; i < n_maps; ++i) {
-        sn_status r = job_allocate(jobs[i], st);
+        sn_status r = job_allocate(jobs[i], st, iterations > 0);
         if (r != SN_OK) return finish(r);
-        sn_mesh *m = jobs[i].mesh;
-        if (iterations > 0 && m->np > 0) {
-            r = pool_alloc((void **)&m->smooth_scratch, sizeof(float) * 3 * (size_t)m->np, m->pool, st,
-                           "smoothing buffer");
-            if (r != SN_OK) return finish(r);
-        }
         if (flags & SN_BATCH_TUNE) {
             r = tune_emit_rows(jobs[i], st, &rows[i]);
             if (r != SN_OK) return finish(r);
         }
+    }
+
+    // the table-driven prologue (cell-centre tables, meta words) and epilogue
+    // (last stencil offsets) of all meshes
+    sn::BatchMeshPrep *prep = nullptr;
+    int64_t prep_entries = 0;
+    {
+        std::vector<sn::BatchMeshPrep> tab((size_t)n_maps);
+        for (int64_t i = 0; i < n_maps; ++i) {
+            const ExtractJob &j = jobs[i];
+            sn::BatchMeshPrep &t = tab[i];
+            std::memset(&t, 0, sizeof(t));
+            t.lut = j.mesh->a.lut_x;
+            t.meta = j.mesh->a.meta;
+            t.sten_tail = j.mesh->a.sten_off + j.mesh->np;
+            t.sten_total = j.s.offS + j.g.Rc;
+            t.nx = j.dims[0];
+            t.ny = j.dims[1];
+            t.start = prep_entries;
+            for (int a = 0; a < 3; ++a) {
+                t.sp[a] = j.spacing[a];
+                t.org[a] = j.origin[a];
+            }
+            prep_entries += j.dims[0] + j.dims[1] + j.dims[2] + 3;
+        }
+        sn_status r = pool_alloc((void **)&prep, sizeof(sn::BatchMeshPrep) * (size_t)n_maps, jobs[0].pool, st,
+                                 "batch prologue table");
+        if (r != SN_OK) return finish(r);
+        jobs[0].temps.push_back(prep);
+        // (a copy from pageable memory: the host vector may go once the call returns)
+        e = cudaMemcpyAsync(prep, tab.data(), sizeof(sn::BatchMeshPrep) * (size_t)n_maps, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return finish(cuda_fail(e, "batch prologue table"));
+    }
+
+    // the sweep table of all meshes (device copy, freed with the scratch)
+    sn::SmoothBatchMap *smooth_table = nullptr;
+    uint32_t *smooth_table_blocks = nullptr;
+    uint32_t total_blocks = 0;
+    if (iterations > 0) {
+        std::vector<sn::SmoothBatchMap> tab((size_t)n_maps);
+        std::vector<uint32_t> starts((size_t)n_maps);
+        const int ppb = sn::smooth_points_per_block();
+        uint64_t nb = 0;
+        for (int64_t i = 0; i < n_maps; ++i) {
+            const sn_mesh *m = jobs[i].mesh;
+            sn::SmoothBatchMap &t = tab[i];
+            std::memset(&t, 0, sizeof(t));
+            t.m = m->a;
+            t.np = m->np;
+            // the first source is chosen so that the last sweep writes m.offsets
+            t.buf[0] = (iterations % 2 == 1) ? m->smooth_scratch : m->a.offsets;
+            t.buf[1] = (iterations % 2 == 1) ? m->a.offsets : m->smooth_scratch;
+            t.spx = (float)m->spacing[0];
+            t.spy = (float)m->spacing[1];
+            t.spz = (float)m->spacing[2];
+            starts[i] = (uint32_t)nb;
+            nb += (uint64_t)((m->np + ppb - 1) / ppb);
+        }
+        if (nb > 0x7fffffffull) return finish(fail(SN_EINVAL, "too many points in one batch"));
+        total_blocks = (uint32_t)nb;
+        const size_t tb = sizeof(sn::SmoothBatchMap) * (size_t)n_maps, sb = sizeof(uint32_t) * (size_t)n_maps;
+        char *d = nullptr;
+        sn_status r = pool_alloc((void **)&d, tb + 256 + sb, jobs[0].pool, st, "sweep table");
+        if (r != SN_OK) return finish(r);
+        jobs[0].temps.push_back(d);
+        smooth_table = reinterpret_cast<sn::SmoothBatchMap *>(d);
+        smooth_table_blocks = reinterpret_cast<uint32_t *>(d + (tb + 255) / 256 * 256);
+        e = cudaMemcpyAsync(smooth_table, tab.data(), tb, cudaMemcpyHostToDevice, st);
+        // (copies from pageable memory: the host vectors may go once the calls return)
+        if (e == cudaSuccess) e = cudaMemcpyAsync(smooth_table_blocks, starts.data(), sb, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return finish(cuda_fail(e, "sweep table"));
     }
 
     // 4. Pass 4 and the smoothing of every map on the side streams, captured
@@ -1153,6 +1268,8 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
             return finish(cuda_fail(e, "graph capture begin"));
         capturing = true;
     }
+    if ((e = sn::launch_prologue_batch(prep, (int)n_maps, prep_entries, origin_st)) != cudaSuccess)
+        return finish(cuda_fail(e, "batch prologue"));
     cudaEvent_t fork2 = nullptr;
     if ((e = event(&fork2)) != cudaSuccess || (e = cudaEventRecord(fork2, origin_st)) != cudaSuccess)
         return finish(cuda_fail(e, "batch fork"));
@@ -1160,20 +1277,22 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
         if ((e = cudaStreamWaitEvent(side[k], fork2, 0)) != cudaSuccess) return finish(cuda_fail(e, "batch fork"));
     const float half = 0.5f * constraint_distance;
     for (int64_t i = 0; i < n_maps; ++i) {
-        cudaStream_t ss = side[i % kBatchStreams];
-        sn_status r = job_emit(jobs[i], ss, rows[i]);
+        sn_status r = job_emit(jobs[i], side[i % kBatchStreams], rows[i], true);
         if (r != SN_OK) return finish(r);
-        sn_mesh *m = jobs[i].mesh;
-        if (iterations > 0 && m->np > 0) {
-            e = sn::launch_smooth(m->a, m->np, iterations, relaxation, half, 0, m->smooth_scratch, m->spacing, ss);
-            if (e != cudaSuccess) return finish(cuda_fail(e, "smoothing launch"));
-        }
     }
     for (int k = 0; k < kBatchStreams; ++k) {
         cudaEvent_t join = nullptr;
         if ((e = event(&join)) != cudaSuccess || (e = cudaEventRecord(join, side[k])) != cudaSuccess ||
             (e = cudaStreamWaitEvent(origin_st, join, 0)) != cudaSuccess)
             return finish(cuda_fail(e, "batch join"));
+    }
+    if ((e = sn::launch_epilogue_batch(prep, (int)n_maps, origin_st)) != cudaSuccess)
+        return finish(cuda_fail(e, "batch epilogue"));
+    // the sweeps of all meshes: one launch per sweep
+    if (iterations > 0 && smooth_table) {
+        e = sn::launch_smooth_batch(smooth_table, smooth_table_blocks, (int)n_maps, total_blocks, iterations,
+                                    relaxation, half, 0, origin_st);
+        if (e != cudaSuccess) return finish(cuda_fail(e, "smoothing launch"));
     }
     if (use_graph) {
         capturing = false;

@@ -38,7 +38,8 @@ cudaError_t emit_tile_t(const void *labels, const Classifier &c, const Geometry 
     // into one graph with different tile shapes all stay within it
     static const int kMaxSmem = (int)(sizeof(uint32_t) * (size_t)TileSmem(kEmitMaxRows, kTileMaxW, kTileMaxW).total);
     if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_emit_tile<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    static std::atomic<uint64_t> done{0};
+    cudaError_t e = smem_limit_once(k_emit_tile<T, MODE>, kMaxSmem, done);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((g.ny + 1 + tg.ty - 1) / tg.ty), (unsigned)(g.nz + 1));
     k_emit_tile<T, MODE><<<grid, 256, smem, st>>>((const T *)labels, c, g, s, m, tot, tg);

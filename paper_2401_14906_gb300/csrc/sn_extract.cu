@@ -426,8 +426,8 @@ cudaError_t count_f(const void *labels, const Classifier &c, const Geometry &g, 
     // one fixed limit for every launch (launch_count rejects tiles above it), so that
     // launches captured into one graph with different tilings all stay within it
     if (smem > kCountMaxSmem) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_count<T, MODE, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kCountMaxSmem);
+    static std::atomic<uint64_t> done{0};
+    cudaError_t e = smem_limit_once(k_count<T, MODE, FAST>, (int)kCountMaxSmem, done);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((g.ny + tl.ty - 1) / tl.ty), (unsigned)((g.nz + tl.kz - 1) / tl.kz));
     k_count<T, MODE, FAST><<<grid, 256, smem, st>>>((const T *)labels, c, g, s, tl, tot);
@@ -456,11 +456,8 @@ cudaError_t count_m(int type, const void *labels, const Classifier &c, const Geo
 // Cell-centre coordinate origin + spacing * (c + 1/2) for c = -1..n-1 on each
 // axis, computed in FP64 with the product and the sum each rounded once, then
 // split into the nearest float (hi) and the float nearest to the remainder (lo).
-__global__ void k_centre_lut(float2 *lut, int64_t nx, int64_t ny, int64_t nz, double3 sp, double3 org)
+__device__ __forceinline__ void centre_entry(float2 *lut, int64_t k, int64_t nx, int64_t ny, double3 sp, double3 org)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t total = nx + ny + nz + 3;
-    if (k >= total) return;
     int64_t c;
     double s, o;
     if (k < nx + 1) {
@@ -481,6 +478,41 @@ __global__ void k_centre_lut(float2 *lut, int64_t nx, int64_t ny, int64_t nz, do
     lut[k] = make_float2(hi, __double2float_rn(__dsub_rn(v, (double)hi)));
 }
 
+__global__ void k_centre_lut(float2 *lut, int64_t nx, int64_t ny, int64_t nz, double3 sp, double3 org)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nx + ny + nz + 3) return;
+    centre_entry(lut, k, nx, ny, sp, org);
+}
+
+// Many meshes: the cell-centre tables of all of them (thread k of the launch is
+// entry k - start of the mesh whose range holds it); the first thread of each
+// mesh also clears its meta words and, once its emission has run (`tails`),
+// copies the stencil total into the last stencil offset.
+__global__ void k_prologue_batch(const BatchMeshPrep *maps, int n, int64_t total)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    int lo = 0;
+    for (int hi = n; hi - lo > 1;) {
+        const int mid = (lo + hi) >> 1;
+        if (maps[mid].start <= k) lo = mid;
+        else hi = mid;
+    }
+    const BatchMeshPrep &p = maps[lo];
+    const int64_t e = k - p.start;
+    centre_entry(p.lut, e, p.nx, p.ny, make_double3(p.sp[0], p.sp[1], p.sp[2]),
+                 make_double3(p.org[0], p.org[1], p.org[2]));
+    if (e == 0)
+        for (int q = 0; q < 4; ++q) p.meta[q] = 0;
+}
+
+__global__ void k_epilogue_batch(const BatchMeshPrep *maps, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) *maps[i].sten_tail = *maps[i].sten_total;
+}
+
 } // namespace
 
 cudaError_t launch_centre_lut(const MeshArrays &m, const int64_t dims[3], const double spacing[3],
@@ -490,6 +522,20 @@ cudaError_t launch_centre_lut(const MeshArrays &m, const int64_t dims[3], const 
     k_centre_lut<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
         m.lut_x, dims[0], dims[1], dims[2], make_double3(spacing[0], spacing[1], spacing[2]),
         make_double3(origin[0], origin[1], origin[2]));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prologue_batch(const BatchMeshPrep *maps, int n, int64_t total_entries, cudaStream_t st)
+{
+    if (n == 0 || total_entries == 0) return cudaSuccess;
+    k_prologue_batch<<<(unsigned)((total_entries + 255) / 256), 256, 0, st>>>(maps, n, total_entries);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_epilogue_batch(const BatchMeshPrep *maps, int n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_epilogue_batch<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(maps, n);
     return cudaGetLastError();
 }
 

@@ -11,6 +11,8 @@
 //   planes).  P plane: bit p of row rc is set iff cell (p-1,cy,cz) has a point.
 #pragma once
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -100,6 +102,20 @@ struct TileGeom {
 };
 
 constexpr int kEmitMaxRows = 32;
+
+// Sets a kernel's dynamic shared-memory limit once per device (`done` is a
+// per-kernel bit set of the devices already done).
+template <typename K> cudaError_t smem_limit_once(K kernel, int bytes, std::atomic<uint64_t> &done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load() & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit);
+    return e;
+}
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
@@ -124,6 +140,19 @@ cudaError_t launch_emit_tile(int type, const void *labels, const Classifier &c, 
                              const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st,
                              int rows = 0);
 
+// Many meshes' cell-centre tables and meta words in one launch, and their last
+// stencil offsets (sten_tail = *sten_total) in another (sn_extract.cu).
+struct BatchMeshPrep {
+    float2 *lut;
+    int32_t *meta;
+    int64_t *sten_tail;
+    const int64_t *sten_total;
+    int64_t nx, ny, start; // start = first table entry of this mesh in the launch
+    double sp[3], org[3];
+};
+cudaError_t launch_prologue_batch(const BatchMeshPrep *maps, int n, int64_t total_entries, cudaStream_t st);
+cudaError_t launch_epilogue_batch(const BatchMeshPrep *maps, int n, cudaStream_t st);
+
 // per-axis cell-centre tables of a mesh (sn_extract.cu)
 cudaError_t launch_centre_lut(const MeshArrays &m, const int64_t dims[3], const double spacing[3],
                               const double origin[3], cudaStream_t st);
@@ -137,6 +166,21 @@ cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float
 // positions in m.points.  iterations == 0 only writes the world positions.
 cudaError_t launch_smooth_from(const MeshArrays &m, int64_t np, int iterations, float relaxation, float half,
                                int sphere, float *start, float *scratch, const double spacing[3], cudaStream_t st);
+
+// The sweeps of many meshes, one launch per sweep over all of them
+// (sn_smooth.cu).  SmoothBatchMap describes one mesh (built on the host,
+// copied to the device); block_start[i] = first sweep block of mesh i.
+struct SmoothBatchMap {
+    MeshArrays m;
+    int64_t np;
+    float *buf[2]; // source of the first sweep, then the other buffer (the result ends in m.offsets)
+    float spx, spy, spz;
+    int pad;
+};
+int smooth_points_per_block();
+cudaError_t launch_smooth_batch(const SmoothBatchMap *maps, const uint32_t *block_start, int n_maps,
+                                uint32_t total_blocks, int iterations, float relaxation, float half, int sphere,
+                                cudaStream_t st);
 
 // learned smoothing proposal (sn_learn.cu); parameters in the layout of sn.h
 constexpr int kLearnParams = 6467;

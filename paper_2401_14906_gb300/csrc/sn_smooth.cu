@@ -28,6 +28,45 @@ __global__ void __launch_bounds__(256) k_centres(MeshArrays m, int64_t np)
     m.points[3 * i + 2] = m.lut_z[(c >> 42) & m21].x;
 }
 
+// One sweep t of many meshes: CTA b works on block b - block_start[i] of the
+// mesh i with block_start[i] <= b < block_start[i+1].
+__global__ void __launch_bounds__(kSweepThreads) k_smooth_batch(const SmoothBatchMap *maps,
+                                                                const uint32_t *block_start, int n, int t,
+                                                                int iterations, float lam, float h, int sphere)
+{
+    const uint32_t b = blockIdx.x;
+    int lo = 0;
+    for (int hi = n; hi - lo > 1;) {
+        const int mid = (lo + hi) >> 1;
+        if (block_start[mid] <= b) lo = mid;
+        else hi = mid;
+    }
+    const SmoothBatchMap &mp = maps[lo];
+    SweepArgs a;
+    a.oin = mp.buf[t & 1];
+    a.oout = mp.buf[(t & 1) ^ 1];
+    a.nbr = mp.m.nbr;
+    a.soff = mp.m.sten_off;
+    a.sids = mp.m.sten_ids;
+    a.fmask = mp.m.face_mask;
+    a.meta = mp.m.meta;
+    a.cells = mp.m.cells;
+    a.lut_x = mp.m.lut_x;
+    a.lut_y = mp.m.lut_y;
+    a.lut_z = mp.m.lut_z;
+    a.points = mp.m.points;
+    a.np = mp.np;
+    a.lam = lam;
+    a.h = h;
+    a.spx = mp.spx;
+    a.spy = mp.spy;
+    a.spz = mp.spz;
+    a.first = t == 0;
+    a.last = t == iterations - 1;
+    a.sphere = sphere;
+    sweep_block<false>(a, (b - block_start[lo]) * (uint32_t)kSweepPoints, a.meta[0] >= kPackedReach);
+}
+
 // world positions from the offsets in `o`
 __global__ void __launch_bounds__(256) k_world(MeshArrays m, const float *o, int64_t np, float spx, float spy,
                                                float spz)
@@ -147,6 +186,27 @@ cudaError_t launch_smooth_from(const MeshArrays &m, int64_t np, int iterations, 
         float *tmp = src;
         src = dst;
         dst = tmp;
+    }
+    return cudaSuccess;
+}
+
+} // namespace sn
+
+namespace sn {
+
+int smooth_points_per_block() { return kSweepPoints; }
+
+cudaError_t launch_smooth_batch(const SmoothBatchMap *maps, const uint32_t *block_start, int n_maps,
+                                uint32_t total_blocks, int iterations, float relaxation, float half, int sphere,
+                                cudaStream_t st)
+{
+    if (n_maps == 0 || total_blocks == 0) return cudaSuccess;
+    for (int t = 0; t < iterations; ++t) {
+        ProfScope ps("k_smooth_batch", st);
+        k_smooth_batch<<<total_blocks, kSweepThreads, 0, st>>>(maps, block_start, n_maps, t, iterations, relaxation,
+                                                               half, sphere);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
