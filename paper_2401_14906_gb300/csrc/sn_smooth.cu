@@ -80,6 +80,27 @@ __global__ void __launch_bounds__(256) k_world(MeshArrays m, const float *o, int
     m.points[3 * i + 2] = world(m.lut_z[(c >> 42) & m21], spz, o[3 * i + 2]);
 }
 
+// Launches sweep `a` on st; `dependent`: as a programmatic dependent of the
+// kernel before it on the stream (the previous sweep), see sweep_block.
+cudaError_t launch_sweep(const SweepArgs &a, unsigned blocks, bool dependent, cudaStream_t st)
+{
+    if (!dependent) {
+        k_smooth<<<blocks, kSweepThreads, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kSweepThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_smooth, a);
+}
+
 } // namespace
 
 cudaError_t launch_centres(const MeshArrays &m, int64_t np, cudaStream_t st)
@@ -126,8 +147,7 @@ cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float
         a.first = t == 0;
         a.last = t == iterations - 1;
         ProfScope ps("k_smooth", st);
-        k_smooth<<<blocks, kSweepThreads, 0, st>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_sweep(a, blocks, t > 0, st)) != cudaSuccess) return e;
         float *tmp = src;
         src = dst;
         dst = tmp;
@@ -180,8 +200,7 @@ cudaError_t launch_smooth_from(const MeshArrays &m, int64_t np, int iterations, 
         a.oout = dst;
         a.last = t == iterations - 1;
         ProfScope ps("k_smooth", st);
-        k_smooth<<<blocks, kSweepThreads, 0, st>>>(a);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_sweep(a, blocks, t > 0, st);
         if (e != cudaSuccess) return e;
         float *tmp = src;
         src = dst;

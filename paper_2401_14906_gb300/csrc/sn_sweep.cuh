@@ -149,11 +149,20 @@ constexpr int kSweepThreads = 256, kSweepPoints = 2 * kSweepThreads; // two poin
 // PPT times as many loads are in flight.  The first sweep starts from zero
 // offsets and reads none.  `csr`: the neighbour distances do not fit the packed
 // record.
+//
+// Sweeps after the first are launched as programmatic dependents of the sweep
+// before them: every block lets the next sweep's blocks be scheduled at once,
+// loads its neighbour records (written by the extraction, never by a sweep),
+// and only then waits for the previous sweep to finish before it reads or
+// writes any offsets.  A launch without that attribute returns from the wait
+// at once.
 template <bool COH, int PPT = 2>
 __device__ __forceinline__ void sweep_block(const SweepArgs &a, uint32_t base, bool csr)
 {
     const uint64_t np = (uint64_t)a.np;
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (csr) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
             const uint32_t i = base + threadIdx.x + q * kSweepThreads;
@@ -166,12 +175,14 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, uint32_t base, b
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         const uint32_t i = base + threadIdx.x + q * kSweepThreads;
+        r[q] = i < np ? a.nbr[i] : make_uint2(0u, 0u);
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const uint32_t i = base + threadIdx.x + q * kSweepThreads;
         o[q] = make_float3(0.f, 0.f, 0.f);
-        r[q] = make_uint2(0u, 0u);
-        if (i < np) {
-            if (!a.first) o[q] = ld3<COH>(a.oin, i);
-            r[q] = a.nbr[i];
-        }
+        if (i < np && !a.first) o[q] = ld3<COH>(a.oin, i);
     }
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
