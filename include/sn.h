@@ -251,6 +251,15 @@ sn_status sn_learner_n_examples(const sn_learner *l, int64_t *n);
  * the last minibatch before its step. */
 sn_status sn_learner_train(sn_learner *l, int epochs, int64_t batch, float lr, float weight_decay, uint64_t seed,
                            float *last_loss);
+/* The tensor-core kernel sn_smooth_learned runs the proposal with:
+ *   SN_LEARN_ENGINE_MMA_SYNC  (default) warp tiles of 16 points carried through
+ *                             all layers in registers (mma.sync m16n8k16);
+ *   SN_LEARN_ENGINE_TCGEN05   tiles of 128 points on tcgen05.mma with the
+ *                             accumulators in tensor memory; producer warps build
+ *                             the features while consumer warps run the layers.
+ * Both give the same results up to the accumulation order. */
+typedef enum { SN_LEARN_ENGINE_MMA_SYNC = 0, SN_LEARN_ENGINE_TCGEN05 = 1 } sn_learn_engine;
+sn_status sn_learner_set_engine(sn_learner *l, sn_learn_engine engine);
 /* The proposal and corrections on a mesh: offsets = clamp(MLP(features)),
  * then `corrections` plain sweeps (relaxation, constraint as for sn_smooth_ex)
  * from there; the world positions follow, as after sn_smooth. */

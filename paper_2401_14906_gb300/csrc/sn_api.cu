@@ -41,6 +41,7 @@ struct sn_learner {
     float *t;                              //           targets [cap][3]
     int64_t n, cap;
     int step;
+    int engine; // SN_LEARN_ENGINE_*
 };
 
 namespace {
@@ -846,6 +847,16 @@ sn_status sn_learner_add_examples(sn_learner *l, const sn_mesh *m, float constra
     return SN_OK;
 }
 
+sn_status sn_learner_set_engine(sn_learner *l, sn_learn_engine engine)
+{
+    g_last_error.clear();
+    if (sn_status r = learner_check(l)) return r;
+    if (engine != SN_LEARN_ENGINE_MMA_SYNC && engine != SN_LEARN_ENGINE_TCGEN05)
+        return fail(SN_EINVAL, "unknown engine");
+    l->engine = (int)engine;
+    return SN_OK;
+}
+
 sn_status sn_learner_n_examples(const sn_learner *l, int64_t *n)
 {
     if (sn_status r = learner_check(l)) return r;
@@ -958,7 +969,7 @@ sn_status sn_smooth_learned(sn_mesh *m, const sn_learner *l, int corrections, fl
     const int sphere = constraint == SN_CONSTRAINT_SPHERE;
     // the proposal lands where an odd or even number of sweeps ends in m.offsets
     float *start = (corrections % 2 == 1) ? m->smooth_scratch : m->a.offsets;
-    e = sn::launch_learn_propose(l->wq, l->params, m->a, start, m->np, half, sphere, m->stream);
+    e = sn::launch_learn_propose(l->wq, l->params, m->a, start, m->np, half, sphere, l->engine, m->stream);
     if (e == cudaSuccess)
         e = sn::launch_smooth_from(m->a, m->np, corrections, relaxation, half, sphere, start,
                                    start == m->a.offsets ? m->smooth_scratch : m->a.offsets, m->spacing, m->stream);

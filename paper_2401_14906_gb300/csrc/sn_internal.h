@@ -189,8 +189,12 @@ cudaError_t launch_learn_quantise(const float *params, uint16_t *wq, cudaStream_
 cudaError_t launch_learn_features(const MeshArrays &m, int64_t np, float half, uint16_t *X, cudaStream_t st);
 cudaError_t launch_learn_forward(const uint16_t *wq, const float *params, const uint16_t *X, int64_t n, float *Y,
                                  cudaStream_t st);
+// engine 0: mma.sync warp tiles (sn_learn.cu); 1: tcgen05 with TMEM accumulators (sn_learn_tc.cu)
 cudaError_t launch_learn_propose(const uint16_t *wq, const float *params, const MeshArrays &m, float *out,
-                                 int64_t np, float half, int sphere, cudaStream_t st);
+                                 int64_t np, float half, int sphere, int engine, cudaStream_t st);
+// the proposal on the tcgen05 tensor cores (sn_learn_tc.cu)
+cudaError_t launch_learn_propose_tc(const uint16_t *wq, const float *params, const MeshArrays &m, float *out,
+                                    int64_t np, float half, int sphere, cudaStream_t st);
 cudaError_t launch_learn_grad(const uint16_t *wq, const float *params, const uint16_t *X, const float *T,
                               int64_t total, int64_t start, int64_t n, uint64_t pa, uint64_t pc, float *grads,
                               float *sse, cudaStream_t st);

@@ -76,7 +76,7 @@ def train(n_maps=200, epochs=4, batch=4096, lr=2e-3, weight_decay=1e-4, iteratio
 
 
 def evaluate(L, labels, spacing=(1.0, 1.0, 1.0), iterations=16, relaxation=0.5, constraint=1.0,
-             corrections=(0, 2, 4), repeats=10):
+             corrections=(0, 2, 4), repeats=10, engines=("mma_sync",)):
     """Plain smoothing vs proposal + k corrections on one map: errors (voxels) and device times (ms)."""
     import torch
     stream = torch.cuda.current_stream()
@@ -97,13 +97,17 @@ def evaluate(L, labels, spacing=(1.0, 1.0, 1.0), iterations=16, relaxation=0.5, 
     ms_plain = timed(lambda: sn.sn_smooth(m, iterations, relaxation, constraint))
     ref = sn.sn_mesh_device_arrays(m)["offsets"].clone()
     out = {"points": np_, "iterations": iterations, "ms_plain": ms_plain, "learned": []}
-    for k in corrections:
-        ms = timed(lambda: sn.sn_smooth_learned(m, L, k, relaxation, constraint))
-        off = sn.sn_mesh_device_arrays(m)["offsets"]
-        err = (off - ref).abs()
-        out["learned"].append({"corrections": k, "ms": ms, "speedup": ms_plain / ms if ms > 0 else None,
-                               "max_err_vox": float(err.max().item()) if np_ else 0.0,
-                               "mean_err_vox": float(err.mean().item()) if np_ else 0.0})
+    for engine in engines:
+        sn.sn_learner_set_engine(L, engine)
+        for k in corrections:
+            ms = timed(lambda: sn.sn_smooth_learned(m, L, k, relaxation, constraint))
+            off = sn.sn_mesh_device_arrays(m)["offsets"]
+            err = (off - ref).abs()
+            out["learned"].append({"engine": engine, "corrections": k, "ms": ms,
+                                   "speedup": ms_plain / ms if ms > 0 else None,
+                                   "max_err_vox": float(err.max().item()) if np_ else 0.0,
+                                   "mean_err_vox": float(err.mean().item()) if np_ else 0.0})
+    sn.sn_learner_set_engine(L, "mma_sync")
     m.free()
     return out
 

@@ -63,6 +63,7 @@ SIGNATURES = {
     "sn_learner_get_params": (ctypes.c_int, [_P, _P]),
     "sn_learner_add_examples": (ctypes.c_int, [_P, _P, ctypes.c_float]),
     "sn_learner_n_examples": (ctypes.c_int, [_P, _I64P]),
+    "sn_learner_set_engine": (ctypes.c_int, [_P, ctypes.c_int]),
     "sn_learner_train": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
                                         ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)]),
     "sn_smooth_learned": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_int]),
@@ -398,6 +399,15 @@ def sn_learner_get_params(learner: Learner):
 
 def sn_learner_add_examples(learner: Learner, mesh: Mesh, constraint_distance=1.0):
     _check(load().sn_learner_add_examples(learner.handle, mesh.handle, float(constraint_distance)))
+
+
+SN_LEARN_ENGINE_MMA_SYNC, SN_LEARN_ENGINE_TCGEN05 = 0, 1
+
+
+def sn_learner_set_engine(learner: Learner, engine):
+    """engine: "mma_sync" (default) or "tcgen05" -- the tensor-core kernel of the proposal."""
+    code = {"mma_sync": SN_LEARN_ENGINE_MMA_SYNC, "tcgen05": SN_LEARN_ENGINE_TCGEN05}.get(engine, engine)
+    _check(load().sn_learner_set_engine(learner.handle, int(code)))
 
 
 def sn_learner_n_examples(learner: Learner):

@@ -187,9 +187,10 @@ def test_training_lowers_the_loss():
     L.free()
 
 
+@pytest.mark.parametrize("engine", ["mma_sync", "tcgen05"])
 @pytest.mark.parametrize("corrections", [0, 1, 2, 3])
 @pytest.mark.parametrize("sphere", [False, True])
-def test_learned_smoothing_matches_oracle(corrections, sphere):
+def test_learned_smoothing_matches_oracle(corrections, sphere, engine):
     sn = _sn()
     w = sn_synth.config1()
     sp = (1.0, 1.5, 0.75)
@@ -197,6 +198,7 @@ def test_learned_smoothing_matches_oracle(corrections, sphere):
     p = _params(8)
     L = sn.sn_learner_create()
     sn.sn_learner_set_params(L, p)
+    sn.sn_learner_set_engine(L, engine)
     m = sn.sn_extract(_dev_labels(w.labels), sp)
     sn.sn_smooth_learned(m, L, corrections, 0.5, 1.0, sphere=sphere)
     got = sn.sn_mesh_copy_to_host(m)
@@ -224,3 +226,37 @@ def test_learned_smoothing_matches_oracle(corrections, sphere):
     centre = ref.points                                # FP64 cell centres (unsmoothed oracle points)
     world = centre + np.array(sp) * off
     np.testing.assert_allclose(got["points"], world, rtol=0, atol=1e-5 * max(sp) + 1e-5)
+
+
+@pytest.mark.parametrize("nx", [1, 3, 6, 11, 24, 40])
+def test_engines_agree_on_ragged_tiles(nx):
+    """Both engines on small random maps whose point counts fall on and between 128-point tiles."""
+    sn = _sn()
+    rng = np.random.default_rng(nx)
+    lab = rng.integers(0, 3, size=(5, 7, nx)).astype(np.uint8)
+    p = _params(9)
+    outs = []
+    for engine in ("mma_sync", "tcgen05"):
+        L = sn.sn_learner_create()
+        sn.sn_learner_set_params(L, p)
+        sn.sn_learner_set_engine(L, engine)
+        m = sn.sn_extract(_dev_labels(lab))
+        sn.sn_smooth_learned(m, L, 0, 0.5, 1.0)
+        outs.append(sn.sn_mesh_copy_to_host(m)["offsets"].astype(np.float64))
+        m.free()
+        L.free()
+    ref = oracle.extract(lab)
+    assert outs[0].shape == outs[1].shape == (ref.n_points, 3) and ref.n_points > 0
+    X = learn.features(ref.stencil_offsets, ref.stencil_ids, ref.face_masks, 1.0)
+    y, bound = _forward_bound(p, X)
+    want = np.clip(y, -0.5, 0.5)
+    for o in outs:
+        assert np.all(np.abs(o - want) <= bound)
+
+
+def test_unknown_engine_rejected():
+    sn = _sn()
+    L = sn.sn_learner_create()
+    with pytest.raises(sn.SNError):
+        sn.sn_learner_set_engine(L, 7)
+    L.free()
