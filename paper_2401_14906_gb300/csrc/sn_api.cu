@@ -29,6 +29,7 @@ struct sn_mesh {
     cudaMemPool_t pool;
     char *arena;        // one block holding the output arrays (and the batch's smoothing buffer)
     size_t arena_bytes;
+    cudaEvent_t extracted; // recorded once the extraction outputs are final (their copies can overlap the smoothing)
 };
 
 struct sn_learner {
@@ -195,11 +196,25 @@ struct ExtractJob {
     bool own_htot = false;
     std::vector<void *> temps;
     sn_mesh *mesh = nullptr;
+    const void *host_labels = nullptr; // labels still to be copied (by job_count, in slabs)
+    size_t lab_bytes = 0;
 };
+
+// the copy stream of this thread on a device (created once, kept)
+cudaStream_t copy_stream(int dev)
+{
+    thread_local std::map<int, cudaStream_t> streams;
+    cudaStream_t &cs = streams[dev];
+    if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        cs = nullptr;
+    }
+    return cs;
+}
 
 sn_status job_prepare(ExtractJob &j, const void *labels, sn_label_type type, const int64_t dims[3],
                       const double spacing[3], const double origin[3], const uint32_t *selected, int64_t n_selected,
-                      uint32_t background, cudaStream_t st)
+                      uint32_t background, cudaStream_t st, bool defer_copy = false)
 {
     if (!labels) return fail(SN_EINVAL, "labels is NULL");
     if (type != SN_U8 && type != SN_U16 && type != SN_U32) return fail(SN_EINVAL, "bad label type");
@@ -256,9 +271,14 @@ sn_status job_prepare(ExtractJob &j, const void *labels, sn_label_type type, con
         void *d = nullptr;
         sn_status r = talloc(&d, lab_bytes, "label copy");
         if (r != SN_OK) return r;
-        e = cudaMemcpyAsync(d, labels, lab_bytes, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return cuda_fail(e, "label copy");
         j.dlabels = d;
+        if (defer_copy) { // job_count copies the labels in slabs that the counting pass follows
+            j.host_labels = labels;
+            j.lab_bytes = lab_bytes;
+        } else {
+            e = cudaMemcpyAsync(d, labels, lab_bytes, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(e, "label copy");
+        }
     }
 
     // classifier (Sec. 3.1)
@@ -351,7 +371,62 @@ sn_status job_count(ExtractJob &j, cudaStream_t st, bool shared_totals = false)
         e = cudaMemsetAsync(j.dtot, 0, sizeof(sn::DevTotals), st);
         if (e != cudaSuccess) return cuda_fail(e, "totals");
     }
-    e = sn::launch_count(j.type, j.dlabels, j.cls, j.g, j.s, j.dtot, st);
+    sn::CountTiling tl;
+    size_t smem = 0;
+    const bool tiled = sn::count_tiling(j.type, j.dlabels, j.g, &tl, &smem);
+    cudaStream_t cs = j.host_labels ? copy_stream(j.dev) : nullptr;
+    if (j.host_labels && tiled && cs && tl.zt1 >= 2) {
+        // host labels: copy them in slabs on the copy stream while the counting
+        // pass runs slab by slab behind them; slab c's tiles also read the first
+        // slice of slab c + 1
+        const int64_t nz_tiles = tl.zt1, K = nz_tiles < 8 ? nz_tiles : 8, per = (nz_tiles + K - 1) / K;
+        const size_t slice = (size_t)j.g.nx * (size_t)j.g.ny * (size_t)j.type;
+        cudaEvent_t ev[9] = {};
+        auto done = [&](sn_status r) {
+            for (cudaEvent_t x : ev)
+                if (x) cudaEventDestroy(x);
+            return r;
+        };
+        for (int c = 0; c <= K; ++c)
+            if ((e = cudaEventCreateWithFlags(&ev[c], cudaEventDisableTiming)) != cudaSuccess)
+                return done(cuda_fail(e, "label slabs"));
+        // the device buffer was allocated on st
+        if ((e = cudaEventRecord(ev[K], st)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev[K], 0)) != cudaSuccess)
+            return done(cuda_fail(e, "label slabs"));
+        if ((e = sn::launch_count_clear(j.g, j.s, st)) != cudaSuccess) return done(cuda_fail(e, "counting launch"));
+        // slab c's count is enqueued right after slab c + 1's copy (pageable host memory is staged by the copy calls)
+        auto count_slab = [&](int64_t c) -> cudaError_t {
+            const int64_t t0 = c * per, t1 = std::min<int64_t>((c + 1) * per, nz_tiles);
+            cudaError_t e2 = cudaStreamWaitEvent(st, ev[c], 0);
+            if (e2 == cudaSuccess && c + 1 < K) e2 = cudaStreamWaitEvent(st, ev[c + 1], 0);
+            if (e2 == cudaSuccess && t1 > t0)
+                e2 = sn::launch_count_range(j.type, j.dlabels, j.cls, j.g, j.s, j.dtot, tl, smem, t0, t1, st);
+            return e2;
+        };
+        for (int64_t c = 0; c < K; ++c) {
+            const int64_t z0 = c * per * tl.kz, z1 = std::min<int64_t>((c + 1) * per * tl.kz, j.g.nz);
+            if (z1 > z0) {
+                e = cudaMemcpyAsync((char *)j.dlabels + (size_t)z0 * slice,
+                                    (const char *)j.host_labels + (size_t)z0 * slice, (size_t)(z1 - z0) * slice,
+                                    cudaMemcpyHostToDevice, cs);
+                if (e != cudaSuccess) return done(cuda_fail(e, "label copy"));
+            }
+            if ((e = cudaEventRecord(ev[c], cs)) != cudaSuccess) return done(cuda_fail(e, "label slabs"));
+            if (c >= 1 && (e = count_slab(c - 1)) != cudaSuccess) return done(cuda_fail(e, "counting launch"));
+        }
+        if ((e = count_slab(K - 1)) != cudaSuccess) return done(cuda_fail(e, "counting launch"));
+        j.host_labels = nullptr;
+        done(SN_OK);
+    } else {
+        if (j.host_labels) { // one copy, then the pass
+            e = cudaMemcpyAsync(const_cast<void *>(j.dlabels), j.host_labels, j.lab_bytes, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(e, "label copy");
+            j.host_labels = nullptr;
+        }
+        e = tiled ? sn::launch_count_clear(j.g, j.s, st) : cudaErrorNotSupported;
+        if (e == cudaSuccess) e = sn::launch_count_range(j.type, j.dlabels, j.cls, j.g, j.s, j.dtot, tl, smem, tl.zt0,
+                                                         tl.zt1, st);
+    }
     if (e == cudaErrorNotSupported) {
         cudaGetLastError();
         if ((e = sn::launch_planes(j.type, j.dlabels, j.cls, j.g, j.s, st)) != cudaSuccess)
@@ -533,7 +608,7 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
     *out = nullptr;
     ExtractJob j;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    sn_status r = job_prepare(j, labels, type, dims, spacing, origin, selected, n_selected, background, st);
+    sn_status r = job_prepare(j, labels, type, dims, spacing, origin, selected, n_selected, background, st, true);
     if (r == SN_OK) r = job_count(j, st);
     if (r == SN_OK) {
         cudaError_t e = cudaStreamSynchronize(st);
@@ -542,6 +617,13 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
     if (r == SN_OK) r = job_allocate(j, st);
     if (r == SN_OK) r = job_emit(j, st, 0);
     if (r == SN_OK) {
+        cudaError_t e = cudaEventCreateWithFlags(&j.mesh->extracted, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(j.mesh->extracted, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (j.mesh->extracted) cudaEventDestroy(j.mesh->extracted);
+            j.mesh->extracted = nullptr; // the copies then simply follow the mesh's stream
+        }
         *out = j.mesh;
         j.mesh = nullptr;
     }
@@ -652,13 +734,32 @@ sn_status sn_mesh_copy_to_host(const sn_mesh *m, float *points, int32_t *quads, 
         {stencil_ids, m->a.sten_ids, sizeof(int32_t) * (size_t)m->ns},
         {offsets, m->a.offsets, sizeof(float) * 3 * (size_t)m->np},
     };
-    for (auto &c : cp) {
-        if (!c.dst || c.bytes == 0) continue;
-        cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, m->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "copy to host");
+    // the extraction outputs (quads, labels, stencils) do not change when the mesh is
+    // smoothed: with the mesh's `extracted` event they are copied on a side stream,
+    // overlapping a smoothing still running on the mesh's stream
+    cudaStream_t side = nullptr;
+    if (m->extracted) {
+        thread_local std::map<int, cudaStream_t> streams;
+        cudaStream_t &cs = streams[m->device];
+        if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            cs = nullptr;
+        }
+        if (cs && cudaStreamWaitEvent(cs, m->extracted, 0) == cudaSuccess) side = cs;
+        else cudaGetLastError();
     }
+    for (int pass = 0; pass < 2; ++pass)
+        for (int k = 0; k < 6; ++k) {
+            auto &c = cp[k];
+            const bool extraction_output = k >= 1 && k <= 4;
+            if (!c.dst || c.bytes == 0 || (pass == 0) != (side && extraction_output)) continue;
+            cudaError_t e =
+                cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, pass == 0 ? side : m->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "copy to host");
+        }
     int32_t meta[4] = {0, 0, 0, 0};
     cudaError_t e = cudaMemcpyAsync(meta, m->a.meta, sizeof(meta), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess && side) e = cudaStreamSynchronize(side);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "copy to host");
     if (meta[1]) return fail(SN_ETIMEOUT, "smoothing dependency wait limit reached");
@@ -677,6 +778,7 @@ void sn_free(sn_mesh *m)
         pool_free(p, m->stream);
     }
     pool_free(m->arena, m->stream);
+    if (m->extracted) cudaEventDestroy(m->extracted);
     std::free(m);
 }
 

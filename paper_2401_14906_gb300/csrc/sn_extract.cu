@@ -133,7 +133,7 @@ template <typename T, int MODE, bool FAST>
 __global__ void __launch_bounds__(256, 4) k_count(const T *__restrict__ lab, Classifier c, Geometry g, ExtractScratch s,
                                                CountTiling tl, DevTotals *tot)
 {
-    count_tile<T, MODE, FAST>(lab, c, g, s, tl, tot, blockIdx.x, blockIdx.y);
+    count_tile<T, MODE, FAST>(lab, c, g, s, tl, tot, blockIdx.x, tl.zt0 + (int64_t)blockIdx.y);
 }
 
 // Single-map scan: tiles are numbered by a ticket in the order blocks start.
@@ -429,7 +429,8 @@ cudaError_t count_f(const void *labels, const Classifier &c, const Geometry &g, 
     static std::atomic<uint64_t> done{0};
     cudaError_t e = smem_limit_once(k_count<T, MODE, FAST>, (int)kCountMaxSmem, done);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((g.ny + tl.ty - 1) / tl.ty), (unsigned)((g.nz + tl.kz - 1) / tl.kz));
+    if (tl.zt1 <= tl.zt0) return cudaSuccess;
+    dim3 grid((unsigned)((g.ny + tl.ty - 1) / tl.ty), (unsigned)(tl.zt1 - tl.zt0));
     k_count<T, MODE, FAST><<<grid, 256, smem, st>>>((const T *)labels, c, g, s, tl, tot);
     return cudaGetLastError();
 }
@@ -539,8 +540,7 @@ cudaError_t launch_epilogue_batch(const BatchMeshPrep *maps, int n, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_count(int type, const void *labels, const Classifier &c, const Geometry &g,
-                         const ExtractScratch &s, DevTotals *tot, cudaStream_t st)
+bool count_tiling(int type, const void *labels, const Geometry &g, CountTiling *out, size_t *smem_out)
 {
     const int64_t row_bytes = g.nx * (int64_t)type;
     constexpr int64_t kSlotBudget = 24 * 1024; // bytes of labels per slot
@@ -557,7 +557,7 @@ cudaError_t launch_count(int type, const void *labels, const Classifier &c, cons
             ty = t;
         }
     }
-    if (ty == 0 || g.W > 4096) return cudaErrorNotSupported;
+    if (ty == 0 || g.W > 4096) return false;
     CountTiling tl;
     tl.ty = ty;
     tl.W = (int)g.W;
@@ -570,15 +570,42 @@ cudaError_t launch_count(int type, const void *labels, const Classifier &c, cons
     if (kz < 4) kz = 4;
     if (kz > 64) kz = 64;
     tl.kz = (int)kz;
+    tl.zt0 = 0;
+    tl.zt1 = (g.nz + kz - 1) / kz;
     // + 256: the packed compares read up to 33 samples past a row's last word
     const size_t smem = kCountHeader + (size_t)kCountSlots * tl.slot_bytes + 2 * 3 * (size_t)(ty + 1) * g.W * 4 + 256;
-    if (smem > kCountMaxSmem) return cudaErrorNotSupported;
-    cudaError_t e = cudaMemsetAsync(s.cntQ, 0, sizeof(int32_t) * (size_t)g.Rc, st);
-    if (e != cudaSuccess) return e;
+    if (smem > kCountMaxSmem) return false;
+    *out = tl;
+    *smem_out = smem;
+    return true;
+}
+
+cudaError_t launch_count_clear(const Geometry &g, const ExtractScratch &s, cudaStream_t st)
+{
+    return cudaMemsetAsync(s.cntQ, 0, sizeof(int32_t) * (size_t)g.Rc, st);
+}
+
+cudaError_t launch_count_range(int type, const void *labels, const Classifier &c, const Geometry &g,
+                               const ExtractScratch &s, DevTotals *tot, CountTiling tl, size_t smem, int64_t zt0,
+                               int64_t zt1, cudaStream_t st)
+{
+    tl.zt0 = zt0;
+    tl.zt1 = zt1;
     ProfScope ps("k_count", st);
     if (c.mode == CLASS_ALL) return count_m<CLASS_ALL>(type, labels, c, g, s, tl, smem, tot, st);
     if (c.mode == CLASS_BITMAP) return count_m<CLASS_BITMAP>(type, labels, c, g, s, tl, smem, tot, st);
     return count_m<CLASS_SORTED>(type, labels, c, g, s, tl, smem, tot, st);
+}
+
+cudaError_t launch_count(int type, const void *labels, const Classifier &c, const Geometry &g,
+                         const ExtractScratch &s, DevTotals *tot, cudaStream_t st)
+{
+    CountTiling tl;
+    size_t smem = 0;
+    if (!count_tiling(type, labels, g, &tl, &smem)) return cudaErrorNotSupported;
+    cudaError_t e = launch_count_clear(g, s, st);
+    if (e != cudaSuccess) return e;
+    return launch_count_range(type, labels, c, g, s, tot, tl, smem, tl.zt0, tl.zt1, st);
 }
 
 cudaError_t launch_planes(int type, const void *labels, const Classifier &c, const Geometry &g,

@@ -91,6 +91,7 @@ struct CountTiling {
     uint64_t wdiv;    // ceil(2^32 / W): it / W == (it * wdiv) >> 32 while it * W < 2^32
     int slot_bytes;   // bytes of one label slot, rounded up to 128
     int aligned;      // rows start on 16-byte boundaries: bulk copies allowed
+    int64_t zt0, zt1; // the launch covers z-tiles [zt0, zt1) (tile z covers slices [z*kz, z*kz + kz], the last one a halo)
 };
 
 // Tiling of the tiled emission (k_emit_tile): TY cell rows of one slice per CTA.
@@ -129,6 +130,14 @@ cudaError_t launch_cellrows(const Geometry &g, const ExtractScratch &s, cudaStre
 // a tile of rows does not fit shared memory (the two kernels above are used then).
 cudaError_t launch_count(int type, const void *labels, const Classifier &c, const Geometry &g,
                          const ExtractScratch &s, DevTotals *tot, cudaStream_t st);
+// The same pass in pieces: the tiling launch_count would use (false: not
+// supported, the two-kernel form is used then), the clearing of the quad counts
+// it starts with, and a launch over z-tiles [zt0, zt1) only.
+bool count_tiling(int type, const void *labels, const Geometry &g, CountTiling *tl, size_t *smem);
+cudaError_t launch_count_clear(const Geometry &g, const ExtractScratch &s, cudaStream_t st);
+cudaError_t launch_count_range(int type, const void *labels, const Classifier &c, const Geometry &g,
+                               const ExtractScratch &s, DevTotals *tot, CountTiling tl, size_t smem, int64_t zt0,
+                               int64_t zt1, cudaStream_t st);
 cudaError_t launch_scan(const Geometry &g, const ExtractScratch &s, DevTotals *totals, cudaStream_t st);
 cudaError_t launch_emit(int type, const void *labels, const Classifier &c, const Geometry &g,
                         const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st);

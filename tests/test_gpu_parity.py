@@ -114,6 +114,13 @@ def test_host_labels_are_copied():
     parity(lab, iterations=8, on_device=False)
 
 
+@pytest.mark.parametrize("dims,dtype", [((64, 64, 64), np.uint16), ((97, 61, 133), np.uint8), ((40, 33, 257), np.uint32)])
+def test_host_labels_uploaded_in_slabs(dims, dtype):
+    """Host labels large enough to be copied in slabs that the counting pass follows slab by slab."""
+    lab = sn_synth.ellipsoids(dims, 6, 5.0, 18.0, dtype, seed=11)
+    parity(lab, iterations=4, on_device=False)
+
+
 def test_zero_iterations_and_zero_relaxation():
     lab = sn_synth.ellipsoids((40, 40, 40), 4, 4.0, 12.0, np.uint16, seed=8)
     parity(lab, iterations=0)
