@@ -346,6 +346,17 @@ def run_ours(args):
         ms_step = ms / args.steps
         value = world * V * args.steps / (ms / 1e3) / 1e9
 
+        # per-step times (events between steps): the median beside the mean above
+        per_step = []
+        for _ in range(args.steps):
+            a_, z_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            step()
+            z_.record(stream)
+            per_step.append((a_, z_))
+        torch.cuda.synchronize()
+        ms_median = statistics.median(a_.elapsed_time(z_) for a_, z_ in per_step)
+
         # per-kernel durations: the same steps again with events around every launch
         sn.sn_profile_read(reset=True)
         sn.sn_profile_enable(True)
@@ -431,7 +442,8 @@ def run_ours(args):
                     "algorithmic_bytes_per_launch": by, "unit_bytes": unit_desc}
     path_time = ms_step / 1e3
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "ms_per_step_median": ms_median,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u%d+f32" % (8 * b), "data": "synthetic",
             "config": workload_config(w, {"parallelism": "replicas" if world > 1 else "single",
                                           "points": P, "quads": Q, "stencil_entries": S}),
