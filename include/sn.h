@@ -314,6 +314,19 @@ sn_status sn_mesh_cells(const sn_mesh *m, const uint64_t **cells);
 sn_status sn_mesh_copy_to_host(const sn_mesh *m, float *points, int32_t *quads, void *quad_labels,
                                int64_t *stencil_offsets, int32_t *stencil_ids, float *offsets);
 
+/* The same copies without waiting: the quads, labels and stencils are copied
+ * as soon as the extraction is done, the points and offsets once the work
+ * enqueued on the mesh's stream so far (the smoothing) is done, on a
+ * library-owned copy stream, so that they overlap later work of the caller
+ * (for instance the next map's upload and extraction).  The host buffers must
+ * be pinned for the copies to run asynchronously, and must stay valid until
+ * sn_mesh_wait returns.  sn_mesh_wait blocks until the last such copy of the
+ * mesh has finished and returns SN_ETIMEOUT as sn_mesh_copy_to_host does.
+ * sn_free may be called with a copy in flight: the memory is released after it. */
+sn_status sn_mesh_copy_to_host_async(sn_mesh *m, float *points, int32_t *quads, void *quad_labels,
+                                     int64_t *stencil_offsets, int32_t *stencil_ids, float *offsets);
+sn_status sn_mesh_wait(sn_mesh *m);
+
 /* Releases the mesh and its device memory (stream-ordered).  NULL is a no-op. */
 void sn_free(sn_mesh *m);
 

@@ -30,6 +30,9 @@ struct sn_mesh {
     char *arena;        // one block holding the output arrays (and the batch's smoothing buffer)
     size_t arena_bytes;
     cudaEvent_t extracted; // recorded once the extraction outputs are final (their copies can overlap the smoothing)
+    cudaEvent_t copied;    // the last sn_mesh_copy_to_host_async has finished
+    int32_t *copy_meta;    // its copy of the meta words (pinned)
+    bool copy_pending;
 };
 
 struct sn_learner {
@@ -766,9 +769,100 @@ sn_status sn_mesh_copy_to_host(const sn_mesh *m, float *points, int32_t *quads, 
     return SN_OK;
 }
 
+// the device-to-host stream of this thread on a device (created once, kept)
+cudaStream_t d2h_stream(int dev)
+{
+    thread_local std::map<int, cudaStream_t> streams;
+    cudaStream_t &cs = streams[dev];
+    if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        cs = nullptr;
+    }
+    return cs;
+}
+
+// pinned slots for the meta words of asynchronous copies, used round robin
+int32_t *meta_slot()
+{
+    constexpr int kSlots = 4096;
+    thread_local int32_t *slots = nullptr;
+    thread_local int next = 0;
+    if (!slots && cudaMallocHost((void **)&slots, sizeof(int32_t) * 4 * kSlots) != cudaSuccess) {
+        cudaGetLastError();
+        slots = nullptr;
+        return nullptr;
+    }
+    int32_t *p = slots + 4 * next;
+    next = (next + 1) % kSlots;
+    return p;
+}
+
+sn_status sn_mesh_copy_to_host_async(sn_mesh *m, float *points, int32_t *quads, void *quad_labels,
+                                     int64_t *stencil_offsets, int32_t *stencil_ids, float *offsets)
+{
+    g_last_error.clear();
+    if (!m) return fail(SN_EINVAL, "mesh is NULL");
+    cudaStream_t cs = d2h_stream(m->device);
+    int32_t *meta = meta_slot();
+    if (!cs || !meta) return fail(SN_ENOMEM, "copy stream or pinned meta slot");
+    cudaError_t e = cudaSuccess;
+    if (!m->copied && (e = cudaEventCreateWithFlags(&m->copied, cudaEventDisableTiming)) != cudaSuccess) {
+        m->copied = nullptr;
+        return cuda_fail(e, "copy event");
+    }
+    cudaEvent_t smoothed = nullptr;
+    if ((e = cudaEventCreateWithFlags(&smoothed, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "copy event");
+    struct {
+        void *dst;
+        const void *src;
+        size_t bytes;
+    } first[] = {
+        {quads, m->a.quads, sizeof(int32_t) * 4 * (size_t)m->nq},
+        {quad_labels, m->a.quad_labels, (size_t)m->type * 2 * (size_t)m->nq},
+        {stencil_offsets, m->a.sten_off, sizeof(int64_t) * (size_t)(m->np + 1)},
+        {stencil_ids, m->a.sten_ids, sizeof(int32_t) * (size_t)m->ns},
+    },
+      then[] = {
+          {points, m->a.points, sizeof(float) * 3 * (size_t)m->np},
+          {offsets, m->a.offsets, sizeof(float) * 3 * (size_t)m->np},
+          {meta, m->a.meta, sizeof(int32_t) * 4},
+      };
+    // extraction outputs once the extraction is done (overlapping a smoothing in flight),
+    // then what the smoothing writes, once the work enqueued on the mesh's stream so far is done
+    e = cudaEventRecord(smoothed, m->stream);
+    if (e == cudaSuccess && m->extracted) e = cudaStreamWaitEvent(cs, m->extracted, 0);
+    if (e == cudaSuccess && !m->extracted) e = cudaStreamWaitEvent(cs, smoothed, 0);
+    for (auto &c : first)
+        if (e == cudaSuccess && c.dst && c.bytes) e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, smoothed, 0);
+    for (auto &c : then)
+        if (e == cudaSuccess && c.dst && c.bytes) e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(m->copied, cs);
+    cudaEventDestroy(smoothed);
+    if (e != cudaSuccess) return cuda_fail(e, "copy to host");
+    m->copy_meta = meta;
+    m->copy_pending = true;
+    return SN_OK;
+}
+
+sn_status sn_mesh_wait(sn_mesh *m)
+{
+    g_last_error.clear();
+    if (!m) return fail(SN_EINVAL, "mesh is NULL");
+    if (!m->copy_pending) return SN_OK;
+    cudaError_t e = cudaEventSynchronize(m->copied);
+    if (e != cudaSuccess) return cuda_fail(e, "copy to host");
+    m->copy_pending = false;
+    if (m->copy_meta && m->copy_meta[1]) return fail(SN_ETIMEOUT, "smoothing dependency wait limit reached");
+    return SN_OK;
+}
+
 void sn_free(sn_mesh *m)
 {
     if (!m) return;
+    // device memory goes back to the pool only after copies still running from it
+    if (m->copied && cudaStreamWaitEvent(m->stream, m->copied, 0) != cudaSuccess) cudaGetLastError();
     void *ps[] = {m->a.points,    m->a.offsets, m->a.cells, m->a.quads, m->a.quad_labels, m->a.sten_off,
                   m->a.sten_ids,  m->a.face_mask, m->a.meta,  m->a.nbr,   m->a.lut_x,       m->smooth_scratch,
                   m->tris};
@@ -779,6 +873,7 @@ void sn_free(sn_mesh *m)
     }
     pool_free(m->arena, m->stream);
     if (m->extracted) cudaEventDestroy(m->extracted);
+    if (m->copied) cudaEventDestroy(m->copied);
     std::free(m);
 }
 

@@ -49,6 +49,8 @@ SIGNATURES = {
     "sn_mesh_face_masks": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
     "sn_mesh_cells": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
     "sn_mesh_copy_to_host": (ctypes.c_int, [_P] + [_P] * 6),
+    "sn_mesh_copy_to_host_async": (ctypes.c_int, [_P] + [_P] * 6),
+    "sn_mesh_wait": (ctypes.c_int, [_P]),
     "sn_free": (None, [_P]),
     "sn_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sn_last_error": (ctypes.c_char_p, []),
@@ -246,6 +248,22 @@ def sn_mesh_copy_to_host(mesh: Mesh):
     order = ["points", "quads", "quad_labels", "stencil_offsets", "stencil_ids", "offsets"]
     _check(load().sn_mesh_copy_to_host(mesh.handle, *[ctypes.c_void_p(out[k].ctypes.data) for k in order]))
     return out
+
+
+def sn_mesh_copy_to_host_async(mesh: Mesh, out):
+    """Starts copying into the caller's pinned buffers `out` (a dict with any of the keys of
+    sn_mesh_copy_to_host, numpy or torch pinned); sn_mesh_wait(mesh) completes it."""
+    order = ["points", "quads", "quad_labels", "stencil_offsets", "stencil_ids", "offsets"]
+
+    def ptr(v):
+        if v is None:
+            return None
+        return ctypes.c_void_p(v.data_ptr() if hasattr(v, "data_ptr") else v.ctypes.data)
+    _check(load().sn_mesh_copy_to_host_async(mesh.handle, *[ptr(out.get(k)) for k in order]))
+
+
+def sn_mesh_wait(mesh: Mesh):
+    _check(load().sn_mesh_wait(mesh.handle))
 
 
 class _CudaArray:

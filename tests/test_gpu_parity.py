@@ -175,3 +175,41 @@ def test_config3_full_size():
     ref = parity(w.labels, w.spacing, w.origin, iterations=w.iterations, relaxation=w.relaxation,
                  constraint=w.constraint)
     assert ref.n_points > 100_000_000
+
+
+def test_async_copy_out_matches_sync_copy():
+    """sn_mesh_copy_to_host_async into pinned buffers, overlapping the next map's extraction, then sn_mesh_wait."""
+    import torch
+    from paper_2401_14906_gb300 import sn
+    labs = [sn_synth.ellipsoids((70, 50, 40), 5, 5.0, 15.0, np.uint16, seed=s) for s in (21, 22)]
+    meshes, outs = [], []
+    for lab in labs:
+        m = sn.sn_extract(lab)                       # host labels
+        sn.sn_smooth(m, 16, 0.5, 1.0)
+        n, q, s = m.counts
+        out = {"points": torch.empty((n, 3), dtype=torch.float32).pin_memory(),
+               "quads": torch.empty((q, 4), dtype=torch.int32).pin_memory(),
+               "quad_labels": torch.empty((q, 2), dtype=torch.int16).pin_memory(),
+               "stencil_offsets": torch.empty(n + 1, dtype=torch.int64).pin_memory(),
+               "stencil_ids": torch.empty(s, dtype=torch.int32).pin_memory(),
+               "offsets": torch.empty((n, 3), dtype=torch.float32).pin_memory()}
+        sn.sn_mesh_copy_to_host_async(m, out)
+        meshes.append(m)
+        outs.append(out)
+    for m, out in zip(meshes, outs):
+        sn.sn_mesh_wait(m)
+        want = sn.sn_mesh_copy_to_host(m)
+        for k, v in out.items():
+            got = v.numpy()
+            if k == "quad_labels":
+                got = got.view(np.uint16)
+            np.testing.assert_array_equal(got, want[k], err_msg=k)
+    # freeing with a copy in flight: the memory goes back after the copy
+    m = sn.sn_extract(labs[0])
+    sn.sn_smooth(m, 16, 0.5, 1.0)
+    n = m.counts[0]
+    pts = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    sn.sn_mesh_copy_to_host_async(m, {"points": pts})
+    sn.sn_mesh_wait(m)
+    m.free()
+    np.testing.assert_array_equal(pts.numpy(), outs[0]["points"].numpy())
