@@ -201,6 +201,7 @@ struct ExtractJob {
     sn_mesh *mesh = nullptr;
     const void *host_labels = nullptr; // labels still to be copied (by job_count, in slabs)
     size_t lab_bytes = 0;
+    bool lab_on_copy_stream = false;   // the label buffer was allocated on the copy stream
 };
 
 // the copy stream of this thread on a device (created once, kept)
@@ -272,7 +273,18 @@ sn_status job_prepare(ExtractJob &j, const void *labels, sn_label_type type, con
     }
     if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
         void *d = nullptr;
-        sn_status r = talloc(&d, lab_bytes, "label copy");
+        // a deferred copy runs on the copy stream: its buffer is allocated there, so that the
+        // upload does not wait for earlier work on the caller's stream (the buffer is freed on
+        // that stream once the counting pass, which waits for the upload, is done)
+        cudaStream_t cs = defer_copy ? copy_stream(j.dev) : nullptr;
+        sn_status r = SN_OK;
+        if (cs) {
+            r = pool_alloc(&d, lab_bytes, j.pool, cs, "label copy");
+            if (r == SN_OK) j.temps.push_back(d);
+            j.lab_on_copy_stream = r == SN_OK;
+        } else {
+            r = talloc(&d, lab_bytes, "label copy");
+        }
         if (r != SN_OK) return r;
         j.dlabels = d;
         if (defer_copy) { // job_count copies the labels in slabs that the counting pass follows
@@ -393,8 +405,9 @@ sn_status job_count(ExtractJob &j, cudaStream_t st, bool shared_totals = false)
         for (int c = 0; c <= K; ++c)
             if ((e = cudaEventCreateWithFlags(&ev[c], cudaEventDisableTiming)) != cudaSuccess)
                 return done(cuda_fail(e, "label slabs"));
-        // the device buffer was allocated on st
-        if ((e = cudaEventRecord(ev[K], st)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev[K], 0)) != cudaSuccess)
+        // a buffer allocated on st is ready for the copy stream only after st's earlier work
+        if (!j.lab_on_copy_stream &&
+            ((e = cudaEventRecord(ev[K], st)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev[K], 0)) != cudaSuccess))
             return done(cuda_fail(e, "label slabs"));
         if ((e = sn::launch_count_clear(j.g, j.s, st)) != cudaSuccess) return done(cuda_fail(e, "counting launch"));
         // slab c's count is enqueued right after slab c + 1's copy (pageable host memory is staged by the copy calls)
@@ -422,6 +435,14 @@ sn_status job_count(ExtractJob &j, cudaStream_t st, bool shared_totals = false)
         done(SN_OK);
     } else {
         if (j.host_labels) { // one copy, then the pass
+            if (j.lab_on_copy_stream && cs) { // the buffer was allocated on the copy stream
+                cudaEvent_t ready = nullptr;
+                e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+                if (e == cudaSuccess) e = cudaEventRecord(ready, cs);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ready, 0);
+                if (ready) cudaEventDestroy(ready);
+                if (e != cudaSuccess) return cuda_fail(e, "label copy");
+            }
             e = cudaMemcpyAsync(const_cast<void *>(j.dlabels), j.host_labels, j.lab_bytes, cudaMemcpyHostToDevice, st);
             if (e != cudaSuccess) return cuda_fail(e, "label copy");
             j.host_labels = nullptr;
