@@ -463,7 +463,8 @@ def run_ours(args):
         if by is not None:
             ach = by / (kernels[dom]["ms_per_launch"] / 1e3) / 1e9
             roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "peak_kind": peak_kind + " (burst copy)", "traffic": traffic_for(dom),
+                    "frac": ach / peak, "peak_kind": peak_kind + " (burst copy)",
+                    "frac_of_nominal_7900": ach / 7900.0, "traffic": traffic_for(dom),
                     "algorithmic_bytes_per_launch": by, "unit_bytes": unit_desc}
     path_time = ms_step / 1e3
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -475,7 +476,8 @@ def run_ours(args):
             "roofline": roof,
             "path_roofline": {"algorithmic_bytes_per_step": alg_total, "bytes_breakdown": alg,
                               "achieved_gbs": alg_total / path_time / 1e9, "peak": peak,
-                              "frac": alg_total / path_time / 1e9 / peak},
+                              "frac": alg_total / path_time / 1e9 / peak,
+                              "frac_of_nominal_7900": alg_total / path_time / 1e9 / 7900.0},
             "kernels": kernels, "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clocks, "e2e": e2e}
     if world == 1 and not args.no_learned:
