@@ -484,7 +484,7 @@ def run_ours(args):
         line["learned"] = learned_comparison(w, args.steps)
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w)
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "host", "paper_cpu_context")}
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -17,7 +17,7 @@
 //     the same way, and the consumers clamp and write the outputs.
 // So the feature gathers of the next tile overlap the MMA chain of this one.
 // The weights stay in shared memory.  All layers reuse TMEM columns [0, 64);
-// each round's TMEM loads finish before the next round's MMAs are issued.
+// each layer's TMEM loads finish before the next layer's MMAs are issued.
 // Every wait is bounded; a wait that gives up flags the mesh (meta[1] bit 1)
 // and ends the CTA's loop after the MMAs in flight have drained.
 //
