@@ -84,12 +84,18 @@ template <bool COH> __device__ __forceinline__ void sweep_point(const SweepArgs 
                              (float)((int)(dpz != 0) - (int)(dmz != 0)));
     // neighbours in face order -x, +x, -y, +y, -z, +z (all offsets are zero before the first sweep)
     if (!a.first) {
-        if (mx) add_diff(acc, ld3<COH>(oin, i - 1), o);
-        if (px) add_diff(acc, ld3<COH>(oin, i + 1), o);
-        if (dmy) add_diff(acc, ld3<COH>(oin, i - dmy), o);
-        if (dpy) add_diff(acc, ld3<COH>(oin, i + dpy), o);
-        if (dmz) add_diff(acc, ld3<COH>(oin, i - dmz), o);
-        if (dpz) add_diff(acc, ld3<COH>(oin, i + dpz), o);
+        float3 sq = make_float3(0.f, 0.f, 0.f);
+        auto add = [&](float3 q) { sq.x += q.x; sq.y += q.y; sq.z += q.z; };
+        if (mx) add(ld3<COH>(oin, i - 1));
+        if (px) add(ld3<COH>(oin, i + 1));
+        if (dmy) add(ld3<COH>(oin, i - dmy));
+        if (dpy) add(ld3<COH>(oin, i + dpy));
+        if (dmz) add(ld3<COH>(oin, i - dmz));
+        if (dpz) add(ld3<COH>(oin, i + dpz));
+        const float fn = (float)n;
+        acc.x += sq.x - fn * o.x;
+        acc.y += sq.y - fn * o.y;
+        acc.z += sq.z - fn * o.z;
     }
     const float ln = a.lam * kInv[n];
     const float3 nv = constrain(make_float3(o.x + ln * acc.x, o.y + ln * acc.y, o.z + ln * acc.z), a.h, a.sphere);
