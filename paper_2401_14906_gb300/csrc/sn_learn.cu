@@ -556,15 +556,11 @@ cudaError_t launch_learn_grad(const uint16_t *wq, const float *params, const uin
                               float *sse, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_learn_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(GradTiles));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    k_learn_grad<<<grid_for(k_learn_grad, n, sizeof(GradTiles)), kLearnThreads, sizeof(GradTiles), st>>>(wq, params, X, T, total, start, n, pa, pc,
-                                                                        grads, sse);
+    static std::atomic<uint64_t> done{0};
+    cudaError_t e = smem_limit_once(k_learn_grad, (int)sizeof(GradTiles), done);
+    if (e != cudaSuccess) return e;
+    k_learn_grad<<<grid_for(k_learn_grad, n, sizeof(GradTiles)), kLearnThreads, sizeof(GradTiles), st>>>(
+        wq, params, X, T, total, start, n, pa, pc, grads, sse);
     return cudaGetLastError();
 }
 
