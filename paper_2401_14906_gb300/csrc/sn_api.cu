@@ -216,9 +216,42 @@ cudaStream_t copy_stream(int dev)
     return cs;
 }
 
+// The scratch arrays of a job, in two groups: those every counting pass must
+// start from zero (quad counts, scan flags and ticket) and the rest.
+struct ScratchItem {
+    void **p;
+    size_t bytes;
+};
+
+void scratch_items(ExtractJob &j, std::vector<ScratchItem> &zero, std::vector<ScratchItem> &rest)
+{
+    const sn::Geometry &g = j.g;
+    sn::ExtractScratch &s = j.s;
+    std::memset(&s, 0, sizeof(s));
+    const int ntiles = (int)((g.Rc + sn::kScanTile - 1) / sn::kScanTile);
+    zero = {
+        {(void **)&s.cntQ, sizeof(int32_t) * (size_t)g.Rc},
+        {(void **)&s.scan_flags, sizeof(int32_t) * (size_t)ntiles},
+        {(void **)&s.scan_ticket, sizeof(uint32_t)},
+    };
+    rest = {
+        {(void **)&s.X, sizeof(uint32_t) * (size_t)(g.Rs * g.WS)},
+        {(void **)&s.Y, sizeof(uint32_t) * (size_t)(g.Rs * g.WS)},
+        {(void **)&s.Z, sizeof(uint32_t) * (size_t)(g.Rs * g.WS)},
+        {(void **)&s.P, sizeof(uint32_t) * (size_t)(g.Rc * g.WS)},
+        {(void **)&s.cntP, sizeof(int32_t) * (size_t)g.Rc},
+        {(void **)&s.cntS, sizeof(int32_t) * (size_t)g.Rc},
+        {(void **)&s.offP, sizeof(int64_t) * (size_t)(g.Rc + 1)},
+        {(void **)&s.offS, sizeof(int64_t) * (size_t)(g.Rc + 1)},
+        {(void **)&s.offQ, sizeof(int64_t) * (size_t)(g.Rc + 1)},
+        {(void **)&s.scan_vals, sizeof(int64_t) * 6 * (size_t)ntiles},
+        {(void **)&j.dtot, sizeof(sn::DevTotals)},
+    };
+}
+
 sn_status job_prepare(ExtractJob &j, const void *labels, sn_label_type type, const int64_t dims[3],
                       const double spacing[3], const double origin[3], const uint32_t *selected, int64_t n_selected,
-                      uint32_t background, cudaStream_t st, bool defer_copy = false)
+                      uint32_t background, cudaStream_t st, bool defer_copy = false, bool alloc_scratch = true)
 {
     if (!labels) return fail(SN_EINVAL, "labels is NULL");
     if (type != SN_U8 && type != SN_U16 && type != SN_U32) return fail(SN_EINVAL, "bad label type");
@@ -336,40 +369,22 @@ sn_status job_prepare(ExtractJob &j, const void *labels, sn_label_type type, con
     g.Rs = ny * nz;
     g.Rc = (ny + 1) * (nz + 1);
     g.lp = nx;
-    const int ntiles = (int)((g.Rc + sn::kScanTile - 1) / sn::kScanTile);
 
-    sn::ExtractScratch &s = j.s;
-    std::memset(&s, 0, sizeof(s));
-    struct {
-        void **p;
-        size_t bytes;
-        const char *what;
-    } plan[] = {
-        {(void **)&s.X, sizeof(uint32_t) * (size_t)(g.Rs * g.WS), "X plane"},
-        {(void **)&s.Y, sizeof(uint32_t) * (size_t)(g.Rs * g.WS), "Y plane"},
-        {(void **)&s.Z, sizeof(uint32_t) * (size_t)(g.Rs * g.WS), "Z plane"},
-        {(void **)&s.P, sizeof(uint32_t) * (size_t)(g.Rc * g.WS), "point plane"},
-        {(void **)&s.cntP, sizeof(int32_t) * (size_t)g.Rc, "point counts"},
-        {(void **)&s.cntS, sizeof(int32_t) * (size_t)g.Rc, "stencil counts"},
-        {(void **)&s.cntQ, sizeof(int32_t) * (size_t)g.Rc, "quad counts"},
-        {(void **)&s.offP, sizeof(int64_t) * (size_t)(g.Rc + 1), "point offsets"},
-        {(void **)&s.offS, sizeof(int64_t) * (size_t)(g.Rc + 1), "stencil offsets"},
-        {(void **)&s.offQ, sizeof(int64_t) * (size_t)(g.Rc + 1), "quad offsets"},
-        {(void **)&s.scan_flags, sizeof(int32_t) * (size_t)ntiles, "scan flags"},
-        {(void **)&s.scan_vals, sizeof(int64_t) * 6 * (size_t)ntiles, "scan values"},
-        {(void **)&s.scan_ticket, sizeof(uint32_t), "scan ticket"},
-        {(void **)&j.dtot, sizeof(sn::DevTotals), "totals"},
-    };
+    if (!alloc_scratch) return SN_OK; // the caller places the scratch (scratch_items)
+    std::vector<ScratchItem> zero, rest;
+    scratch_items(j, zero, rest);
     // one block for all of them, each array on a 256-byte boundary
     size_t total = 0;
-    for (auto &pl : plan) total += (pl.bytes + 255) / 256 * 256;
+    for (auto *v : {&zero, &rest})
+        for (auto &it : *v) total += (it.bytes + 255) / 256 * 256;
     char *block = nullptr;
     sn_status r = talloc((void **)&block, total, "extraction scratch");
     if (r != SN_OK) return r;
-    for (auto &pl : plan) {
-        *pl.p = block;
-        block += (pl.bytes + 255) / 256 * 256;
-    }
+    for (auto *v : {&zero, &rest})
+        for (auto &it : *v) {
+            *it.p = block;
+            block += (it.bytes + 255) / 256 * 256;
+        }
     return SN_OK;
 }
 
@@ -377,6 +392,8 @@ sn_status job_prepare(ExtractJob &j, const void *labels, sn_label_type type, con
 // the scan; the totals land in j.htot once the stream reaches this point.
 sn_status job_count(ExtractJob &j, cudaStream_t st, bool shared_totals = false)
 {
+    // shared_totals (the batched call): the caller clears the totals, quad counts,
+    // scan flags and tickets of all jobs at once and reads the totals back at once
     cudaError_t e = cudaSuccess;
     if (!shared_totals) { // else the caller clears and reads back the totals of many jobs at once
         if (!j.htot) {
@@ -409,7 +426,8 @@ sn_status job_count(ExtractJob &j, cudaStream_t st, bool shared_totals = false)
         if (!j.lab_on_copy_stream &&
             ((e = cudaEventRecord(ev[K], st)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev[K], 0)) != cudaSuccess))
             return done(cuda_fail(e, "label slabs"));
-        if ((e = sn::launch_count_clear(j.g, j.s, st)) != cudaSuccess) return done(cuda_fail(e, "counting launch"));
+        if (!shared_totals && (e = sn::launch_count_clear(j.g, j.s, st)) != cudaSuccess)
+            return done(cuda_fail(e, "counting launch"));
         // slab c's count is enqueued right after slab c + 1's copy (pageable host memory is staged by the copy calls)
         auto count_slab = [&](int64_t c) -> cudaError_t {
             const int64_t t0 = c * per, t1 = std::min<int64_t>((c + 1) * per, nz_tiles);
@@ -447,7 +465,7 @@ sn_status job_count(ExtractJob &j, cudaStream_t st, bool shared_totals = false)
             if (e != cudaSuccess) return cuda_fail(e, "label copy");
             j.host_labels = nullptr;
         }
-        e = tiled ? sn::launch_count_clear(j.g, j.s, st) : cudaErrorNotSupported;
+        e = !tiled ? cudaErrorNotSupported : shared_totals ? cudaSuccess : sn::launch_count_clear(j.g, j.s, st);
         if (e == cudaSuccess) e = sn::launch_count_range(j.type, j.dlabels, j.cls, j.g, j.s, j.dtot, tl, smem, tl.zt0,
                                                          tl.zt1, st);
     }
@@ -458,7 +476,7 @@ sn_status job_count(ExtractJob &j, cudaStream_t st, bool shared_totals = false)
         e = sn::launch_cellrows(j.g, j.s, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "counting launch");
-    if ((e = sn::launch_scan(j.g, j.s, j.dtot, st)) != cudaSuccess) return cuda_fail(e, "k_scan launch");
+    if ((e = sn::launch_scan(j.g, j.s, j.dtot, st, !shared_totals)) != cudaSuccess) return cuda_fail(e, "k_scan launch");
     if (!shared_totals) {
         e = cudaMemcpyAsync(j.htot, j.dtot, sizeof(sn::DevTotals), cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_fail(e, "count read-back");
@@ -1363,11 +1381,35 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
     };
     const double one[3] = {1.0, 1.0, 1.0}, zero[3] = {0.0, 0.0, 0.0};
 
-    // 1. checks, label copies, scratch (main stream)
+    // 1. checks and label copies (main stream), then the scratch of all maps in one block
+    //    whose first part (quad counts, scan flags and tickets of every map) is cleared at once
     for (int64_t i = 0; i < n_maps; ++i) {
         sn_status r = job_prepare(jobs[i], labels[i], types[i], dims + 3 * i, spacing ? spacing + 3 * i : one,
-                                  origin ? origin + 3 * i : zero, nullptr, 0, background, st);
+                                  origin ? origin + 3 * i : zero, nullptr, 0, background, st, false, false);
         if (r != SN_OK) return finish(r);
+    }
+    {
+        std::vector<ScratchItem> zero_items, rest_items, z, rr;
+        for (int64_t i = 0; i < n_maps; ++i) {
+            scratch_items(jobs[i], z, rr);
+            zero_items.insert(zero_items.end(), z.begin(), z.end());
+            rest_items.insert(rest_items.end(), rr.begin(), rr.end());
+        }
+        size_t zbytes = 0, total = 0;
+        for (auto &it : zero_items) zbytes += (it.bytes + 255) / 256 * 256;
+        total = zbytes;
+        for (auto &it : rest_items) total += (it.bytes + 255) / 256 * 256;
+        char *block = nullptr;
+        sn_status r = pool_alloc((void **)&block, total, jobs[0].pool, st, "batch scratch");
+        if (r != SN_OK) return finish(r);
+        jobs[0].temps.push_back(block);
+        char *at = block;
+        for (auto *v : {&zero_items, &rest_items})
+            for (auto &it : *v) {
+                *it.p = at;
+                at += (it.bytes + 255) / 256 * 256;
+            }
+        if ((e = cudaMemsetAsync(block, 0, zbytes, st)) != cudaSuccess) return finish(cuda_fail(e, "batch scratch"));
     }
     if (!(htot = batch_totals(n_maps))) return finish(fail(SN_ENOMEM, "pinned totals"));
     // the device totals of all maps in one array: one clear, one read-back

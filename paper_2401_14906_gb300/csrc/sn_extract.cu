@@ -625,13 +625,14 @@ cudaError_t launch_cellrows(const Geometry &g, const ExtractScratch &s, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan(const Geometry &g, const ExtractScratch &s, DevTotals *totals, cudaStream_t st)
+cudaError_t launch_scan(const Geometry &g, const ExtractScratch &s, DevTotals *totals, cudaStream_t st, bool clear)
 {
     const int ntiles = (int)((g.Rc + kScanTile - 1) / kScanTile);
-    cudaError_t e = cudaMemsetAsync(s.scan_flags, 0, sizeof(int32_t) * (size_t)ntiles, st);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(s.scan_ticket, 0, sizeof(uint32_t), st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (clear) {
+        if ((e = cudaMemsetAsync(s.scan_flags, 0, sizeof(int32_t) * (size_t)ntiles, st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(s.scan_ticket, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+    }
     ProfScope ps("k_scan", st);
     k_scan<<<ntiles, kScanThreads, 0, st>>>(g, s, totals, ntiles);
     return cudaGetLastError();

@@ -138,7 +138,9 @@ cudaError_t launch_count_clear(const Geometry &g, const ExtractScratch &s, cudaS
 cudaError_t launch_count_range(int type, const void *labels, const Classifier &c, const Geometry &g,
                                const ExtractScratch &s, DevTotals *tot, CountTiling tl, size_t smem, int64_t zt0,
                                int64_t zt1, cudaStream_t st);
-cudaError_t launch_scan(const Geometry &g, const ExtractScratch &s, DevTotals *totals, cudaStream_t st);
+// clear = false: the scan flags and ticket are already zero
+cudaError_t launch_scan(const Geometry &g, const ExtractScratch &s, DevTotals *totals, cudaStream_t st,
+                        bool clear = true);
 cudaError_t launch_emit(int type, const void *labels, const Classifier &c, const Geometry &g,
                         const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st);
 
