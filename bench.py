@@ -499,7 +499,7 @@ def learned_comparison(w, repeats):
         return {"unavailable": "no trained parameters (python -m paper_2401_14906_gb300.proposal)"}
     L = proposal.load_learner()
     r = proposal.evaluate(L, w.labels, w.spacing, w.iterations, w.relaxation, w.constraint,
-                          corrections=(0, 1, 2, 4), repeats=max(3, repeats), engines=("mma_sync", "tcgen05"))
+                          corrections=(0, 1, 2, 4, 8), repeats=max(3, repeats), engines=("mma_sync", "tcgen05"))
     L.free()
     target = {"max_err_vox": 1e-3, "speedup_vs_plain": 2.0}
     met = [c for c in r["learned"]
