@@ -107,13 +107,16 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
         pl_lo[dk] = lo;
         pl_hi[dk] = hi;
     }
-    for (int it = tid; it < NS * WS; it += nthr) {
-        const int slot = it / WS, dz = slot / (TY + 2), lr = slot - dz * (TY + 2) - 1;
-        if (lr < pr_lo[dz] || lr >= pr_hi[dz]) sP[it] = 0u;
+    // rows outside the volume (no copy lands there) are zeroed, one thread per row
+    for (int slot = tid; slot < NS; slot += nthr) {
+        const int dz = slot / (TY + 2), lr = slot - dz * (TY + 2) - 1;
+        if (lr < pr_lo[dz] || lr >= pr_hi[dz])
+            for (int w = 0; w < WS; ++w) sP[slot * WS + w] = 0u;
     }
-    for (int it = tid; it < 6 * (TY + 1) * WS; it += nthr) {
-        const int r = it / WS, dk = r / (3 * (TY + 1)), lr = r % (TY + 1);
-        if (lr < pl_lo[dk] || lr >= pl_hi[dk]) sPl[it] = 0u;
+    for (int r = tid; r < 6 * (TY + 1); r += nthr) {
+        const int dk = r / (3 * (TY + 1)), lr = r % (TY + 1);
+        if (lr < pl_lo[dk] || lr >= pl_hi[dk])
+            for (int w = 0; w < WS; ++w) sPl[r * WS + w] = 0u;
     }
     if (tid == 0) {
         mbar_init(bar, 1);
