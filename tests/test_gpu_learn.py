@@ -260,3 +260,29 @@ def test_unknown_engine_rejected():
     with pytest.raises(sn.SNError):
         sn.sn_learner_set_engine(L, 7)
     L.free()
+
+
+@pytest.mark.parametrize("engine", ["mma_sync", "tcgen05"])
+def test_degenerate_meshes(engine):
+    """No points at all, and the 8 points of a single voxel (one partial tile of either engine)."""
+    sn = _sn()
+    L = sn.sn_learner_create()
+    p = _params(10)
+    sn.sn_learner_set_params(L, p)
+    sn.sn_learner_set_engine(L, engine)
+    empty = sn.sn_extract(_dev_labels(np.zeros((3, 4, 5), np.uint16)))
+    sn.sn_smooth_learned(empty, L, 2, 0.5, 1.0)
+    assert empty.counts == (0, 0, 0)
+    empty.free()
+    lab = np.zeros((3, 3, 3), np.uint16)
+    lab[1, 1, 1] = 5
+    m = sn.sn_extract(_dev_labels(lab))
+    sn.sn_smooth_learned(m, L, 0, 0.5, 1.0)
+    got = sn.sn_mesh_copy_to_host(m)["offsets"].astype(np.float64)
+    m.free()
+    L.free()
+    ref = oracle.extract(lab)
+    X = learn.features(ref.stencil_offsets, ref.stencil_ids, ref.face_masks, 1.0)
+    y, bound = _forward_bound(p, X)
+    assert got.shape == (8, 3)
+    assert np.all(np.abs(got - np.clip(y, -0.5, 0.5)) <= bound)
