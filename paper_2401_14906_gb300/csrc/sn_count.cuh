@@ -19,8 +19,9 @@ namespace dev {
 // rows (cy, cz) with their point and stencil counts (Pass 3).  Every label is
 // read from HBM once; halo rows and the halo slice come from L2.
 constexpr int kCountSlots = 3;
-constexpr int kCountMaxTY = 64;    // rows per tile, at most (the single-map heuristic stops at 16)
-constexpr int kCountHeader = 1024; // mbarriers (24 B) + row counters (3*64+2 ints) fit in 1024 bytes
+constexpr int kCountMaxTY = 16;    // rows per tile, at most
+constexpr int kCountHeader = 1024; // mbarriers (24 B) + two sets of row counters (2 * (3*16+2) ints) fit in 1024 bytes
+static_assert(32 + 2 * (3 * kCountMaxTY + 2) * 4 <= kCountHeader, "row counters overflow the header");
 
 // --- edge words of 32 samples from rows in shared memory, packed-integer form.
 // flags16(x): bit 15 / bit 31 set iff the low / high 16-bit half of x is
@@ -32,115 +33,144 @@ __device__ __forceinline__ uint32_t flags8(uint32_t x) { return ((x & 0x7f7f7f7f
 __device__ __forceinline__ uint32_t nibble(uint32_t u) { return (((u >> 7) & 0x01010101u) * 0x01020408u) >> 24; }
 
 
-// Difference mask of 32 samples of `a` against 32 samples of `b` (or, with
-// SHIFT, against `a` one sample further on).  Samples are read from shared
-// memory as 16-byte vectors; a is followed by at least 4 more bytes.
-template <typename T, bool SHIFT> struct Differ;
-
-template <bool SHIFT> struct Differ<uint16_t, SHIFT> {
-    __device__ static __forceinline__ uint32_t run(const uint16_t *a, const uint16_t *b)
-    {
-        const uint4 *a4 = reinterpret_cast<const uint4 *>(a), *b4 = reinterpret_cast<const uint4 *>(b);
-        uint32_t x[16], any = 0;
-        uint4 na = a4[0];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint4 va = na;
-            uint4 vb;
-            if (SHIFT) {
-                const uint32_t nxt = q < 3 ? (na = a4[q + 1]).x : reinterpret_cast<const uint32_t *>(a)[16];
-                vb = make_uint4(__byte_perm(va.x, va.y, 0x5432), __byte_perm(va.y, va.z, 0x5432),
-                                __byte_perm(va.z, va.w, 0x5432), __byte_perm(va.w, nxt, 0x5432));
-            } else {
-                if (q < 3) na = a4[q + 1];
-                vb = b4[q];
-            }
-            x[4 * q + 0] = va.x ^ vb.x;
-            x[4 * q + 1] = va.y ^ vb.y;
-            x[4 * q + 2] = va.z ^ vb.z;
-            x[4 * q + 3] = va.w ^ vb.w;
-            any |= x[4 * q] | x[4 * q + 1] | x[4 * q + 2] | x[4 * q + 3];
-        }
-        if (!any) return 0u;
-        uint32_t m = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            m |= nibble(__byte_perm(flags16(x[2 * q]), flags16(x[2 * q + 1]), 0x7531)) << (4 * q);
-        return m;
-    }
+// A thread compares the 32 samples of one word (2 * sizeof(T) chunks of 16
+// bytes), and the lanes of a warp hold consecutive words, so the chunk q of
+// eight consecutive words falls into at most 8 / (2 * sizeof(T)) of the eight
+// 16-byte bank groups.  Each thread therefore reads its chunks in an order
+// rotated by its word index: slot q holds chunk (q + rot) mod C, and the eight
+// threads of a quarter-warp read eight different bank groups.  The mask bits
+// of slot q are assembled at bit BITS * q and rotated into place at the end.
+template <typename T> struct WordChunks {
+    static constexpr int C = 2 * (int)sizeof(T);     // 16-byte chunks per word
+    static constexpr int BITS = 16 / (int)sizeof(T); // samples (mask bits) per chunk
+    static constexpr int LANES = 8 / C;              // consecutive words sharing a rotation
+    __device__ static __forceinline__ int rot(int w) { return (w / LANES) & (C - 1); }
 };
 
-template <bool SHIFT> struct Differ<uint8_t, SHIFT> {
-    __device__ static __forceinline__ uint32_t run(const uint8_t *a, const uint8_t *b)
-    {
-        const uint4 *a4 = reinterpret_cast<const uint4 *>(a), *b4 = reinterpret_cast<const uint4 *>(b);
-        uint32_t x[8], any = 0;
-        const uint4 v0 = a4[0], v1 = a4[1];
-        uint4 w0, w1;
-        if (SHIFT) {
-            const uint32_t nxt = reinterpret_cast<const uint32_t *>(a)[8];
-            w0 = make_uint4(__byte_perm(v0.x, v0.y, 0x4321), __byte_perm(v0.y, v0.z, 0x4321),
-                            __byte_perm(v0.z, v0.w, 0x4321), __byte_perm(v0.w, v1.x, 0x4321));
-            w1 = make_uint4(__byte_perm(v1.x, v1.y, 0x4321), __byte_perm(v1.y, v1.z, 0x4321),
-                            __byte_perm(v1.z, v1.w, 0x4321), __byte_perm(v1.w, nxt, 0x4321));
-        } else {
-            w0 = b4[0];
-            w1 = b4[1];
-        }
-        x[0] = v0.x ^ w0.x; x[1] = v0.y ^ w0.y; x[2] = v0.z ^ w0.z; x[3] = v0.w ^ w0.w;
-        x[4] = v1.x ^ w1.x; x[5] = v1.y ^ w1.y; x[6] = v1.z ^ w1.z; x[7] = v1.w ^ w1.w;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) any |= x[k];
-        if (!any) return 0u;
-        uint32_t m = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) m |= nibble(flags8(x[k])) << (4 * k);
-        return m;
-    }
-};
+// mask bit e set iff sample e of a xor-ed chunk is nonzero
+template <typename T> __device__ __forceinline__ uint32_t chunk_bits(uint4 x);
+template <> __device__ __forceinline__ uint32_t chunk_bits<uint16_t>(uint4 x)
+{
+    return nibble(__byte_perm(flags16(x.x), flags16(x.y), 0x7531)) |
+           (nibble(__byte_perm(flags16(x.z), flags16(x.w), 0x7531)) << 4);
+}
+template <> __device__ __forceinline__ uint32_t chunk_bits<uint8_t>(uint4 x)
+{
+    return nibble(flags8(x.x)) | (nibble(flags8(x.y)) << 4) | (nibble(flags8(x.z)) << 8) | (nibble(flags8(x.w)) << 12);
+}
+template <> __device__ __forceinline__ uint32_t chunk_bits<uint32_t>(uint4 x)
+{
+    return (uint32_t)(x.x != 0u) | ((uint32_t)(x.y != 0u) << 1) | ((uint32_t)(x.z != 0u) << 2) |
+           ((uint32_t)(x.w != 0u) << 3);
+}
 
-template <bool SHIFT> struct Differ<uint32_t, SHIFT> {
-    __device__ static __forceinline__ uint32_t run(const uint32_t *a, const uint32_t *b)
-    {
-        const uint4 *a4 = reinterpret_cast<const uint4 *>(a), *b4 = reinterpret_cast<const uint4 *>(b);
+// a chunk moved down by one sample, the top sample taken from the first 4 bytes of the next chunk
+template <typename T> __device__ __forceinline__ uint4 shift1(uint4 v, uint32_t nxt);
+template <> __device__ __forceinline__ uint4 shift1<uint16_t>(uint4 v, uint32_t nxt)
+{
+    return make_uint4(__byte_perm(v.x, v.y, 0x5432), __byte_perm(v.y, v.z, 0x5432), __byte_perm(v.z, v.w, 0x5432),
+                      __byte_perm(v.w, nxt, 0x5432));
+}
+template <> __device__ __forceinline__ uint4 shift1<uint8_t>(uint4 v, uint32_t nxt)
+{
+    return make_uint4(__byte_perm(v.x, v.y, 0x4321), __byte_perm(v.y, v.z, 0x4321), __byte_perm(v.z, v.w, 0x4321),
+                      __byte_perm(v.w, nxt, 0x4321));
+}
+template <> __device__ __forceinline__ uint4 shift1<uint32_t>(uint4 v, uint32_t nxt)
+{
+    return make_uint4(v.y, v.z, v.w, nxt);
+}
+
+__device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) { return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w); }
+__device__ __forceinline__ uint32_t or4(uint4 a) { return a.x | a.y | a.z | a.w; }
+
+// Difference mask of the slots va (rotation rot) against the same chunks of
+// the row at b; 0 without a single differing sample.
+template <typename T>
+__device__ __forceinline__ uint32_t differ_rows(const uint4 (&va)[WordChunks<T>::C], const T *b, int rot)
+{
+    constexpr int C = WordChunks<T>::C, BITS = WordChunks<T>::BITS;
+    const uint4 *b4 = reinterpret_cast<const uint4 *>(b);
+    if (sizeof(T) == 4) { // four compares per chunk: no early-out, no xor-ed chunks kept
         uint32_t m = 0;
-        uint4 na = a4[0];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const uint4 va = na;
-            uint4 vb;
-            if (SHIFT) {
-                const uint32_t nxt = q < 7 ? (na = a4[q + 1]).x : a[32];
-                vb = make_uint4(va.y, va.z, va.w, nxt);
-            } else {
-                if (q < 7) na = a4[q + 1];
-                vb = b4[q];
-            }
-            m |= ((uint32_t)(va.x != vb.x) | ((uint32_t)(va.y != vb.y) << 1) | ((uint32_t)(va.z != vb.z) << 2) |
-                  ((uint32_t)(va.w != vb.w) << 3))
-                 << (4 * q);
-        }
-        return m;
+        for (int q = 0; q < C; ++q) m |= chunk_bits<T>(xor4(va[q], b4[(q + rot) & (C - 1)])) << (BITS * q);
+        return __funnelshift_l(m, m, BITS * rot);
     }
-};
+    uint4 x[C];
+    uint32_t any = 0;
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+        x[q] = xor4(va[q], b4[(q + rot) & (C - 1)]);
+        any |= or4(x[q]);
+    }
+    if (!any) return 0u;
+    uint32_t m = 0;
+#pragma unroll
+    for (int q = 0; q < C; ++q) m |= chunk_bits<T>(x[q]) << (BITS * q);
+    return __funnelshift_l(m, m, BITS * rot);
+}
 
 // X/Y/Z words of samples [32w, 32w+32) of a row held in shared memory.
 // Fast form (every value its own class, rows on 16-byte boundaries): packed
-// compares; otherwise one classified sample at a time.
+// compares over rotated 16-byte chunks; the row's chunks are read once for all
+// three words, and the sample after the word comes from the next lane, which
+// holds word w+1 of the same row (it matters only when w+1 < W: the x-edge
+// mask drops bit 31 of the last word).  Called by every lane of the warp
+// (`in` false: no loads, zero words).
 template <typename T, int MODE, bool FAST>
 __device__ __forceinline__ void edge_words(const Classifier &c, const T *row, const T *rowY, const T *rowZ, int64_t nx,
-                                           int w, bool doY, bool doZ, uint32_t &X, uint32_t &Y, uint32_t &Z)
+                                           int w, int W, int lane, bool in, bool doY, bool doZ, uint32_t &X,
+                                           uint32_t &Y, uint32_t &Z)
 {
     const int i0 = w * 32;
     const int nv = (int)(nx - i0); // valid samples in this word (may exceed 32)
     const uint32_t mv = nv >= 32 ? 0xffffffffu : (nv <= 0 ? 0u : ((1u << nv) - 1u));
     const uint32_t mx = nv - 1 >= 32 ? 0xffffffffu : (nv - 1 <= 0 ? 0u : ((1u << (nv - 1)) - 1u));
     if (FAST) {
-        X = Differ<T, true>::run(row + i0, nullptr) & mx;
-        Y = doY ? (Differ<T, false>::run(row + i0, rowY + i0) & mv) : 0u;
-        Z = doZ ? (Differ<T, false>::run(row + i0, rowZ + i0) & mv) : 0u;
+        constexpr int C = WordChunks<T>::C, BITS = WordChunks<T>::BITS;
+        const int rot = WordChunks<T>::rot(w);
+        const uint4 *a4 = reinterpret_cast<const uint4 *>(row + i0);
+        uint4 va[C];
+        uint32_t first = 0; // first 4 bytes of chunk 0
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            va[q] = in ? a4[(q + rot) & (C - 1)] : make_uint4(0u, 0u, 0u, 0u);
+            if (((q + rot) & (C - 1)) == 0) first = va[q].x;
+        }
+        uint32_t nxt = __shfl_down_sync(kFull, first, 1);
+        if (lane == 31 && in && w + 1 < W) nxt = *reinterpret_cast<const uint32_t *>(row + i0 + 32);
+        X = Y = Z = 0u;
+        if (!in) return;
+        if (sizeof(T) == 4) {
+            uint32_t m = 0;
+#pragma unroll
+            for (int q = 0; q < C; ++q) {
+                const uint32_t n = ((q + rot) & (C - 1)) == C - 1 ? nxt : va[(q + 1) & (C - 1)].x;
+                m |= chunk_bits<T>(xor4(va[q], shift1<T>(va[q], n))) << (BITS * q);
+            }
+            X = __funnelshift_l(m, m, BITS * rot) & mx;
+        } else {
+            uint4 x[C];
+            uint32_t any = 0;
+#pragma unroll
+            for (int q = 0; q < C; ++q) {
+                const uint32_t n = ((q + rot) & (C - 1)) == C - 1 ? nxt : va[(q + 1) & (C - 1)].x;
+                x[q] = xor4(va[q], shift1<T>(va[q], n));
+                any |= or4(x[q]);
+            }
+            if (any) {
+                uint32_t m = 0;
+#pragma unroll
+                for (int q = 0; q < C; ++q) m |= chunk_bits<T>(x[q]) << (BITS * q);
+                X = __funnelshift_l(m, m, BITS * rot) & mx;
+            }
+        }
+        if (doY) Y = differ_rows<T>(va, rowY + i0, rot) & mv;
+        if (doZ) Z = differ_rows<T>(va, rowZ + i0, rot) & mv;
     } else {
         X = Y = Z = 0u;
+        if (!in) return;
         for (int b = 0; b < 32; ++b) {
             const int64_t i = i0 + b;
             if (i >= nx) break;
@@ -161,7 +191,7 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
                                            int64_t by)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    const int TY = tl.ty, W = tl.W, tid = threadIdx.x, nthr = blockDim.x;
+    const int TY = tl.ty, W = tl.W, tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
     const int64_t nx = g.nx, ny = g.ny, nz = g.nz, lp = g.lp;
     const int64_t j0 = bx * TY, k0 = by * tl.kz;
     const int rows_ld = (int)((j0 + TY + 1 <= ny) ? TY + 1 : ny - j0); // rows of a slice block
@@ -171,7 +201,7 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
     const int extra = (j0 == 0) ? 1 : 0;                                 // the first tile also owns cy = -1
 
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-    int32_t *cnt = reinterpret_cast<int32_t *>(smem + 32); // [0..TY): quads, [TY..2TY+1): points, [..): stencil
+    int32_t *cnt = reinterpret_cast<int32_t *>(smem + 32); // per set: [0..TY) quads, [TY..2TY+1) points, [..) stencil
     uint8_t *slots = smem + kCountHeader;
     uint32_t *planes = reinterpret_cast<uint32_t *>(slots + (size_t)kCountSlots * tl.slot_bytes);
     const int plane_words = 3 * (TY + 1) * W;
@@ -209,10 +239,26 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
     uint32_t phase_bits = 0; // parity of the next completion of each slot
     bool failed = false;
     int cur = 0;
+    // Two sets of row counters, used by alternate steps: a step's quad counts are
+    // read after its second barrier, and its point and stencil counts after the
+    // first barrier of the next step (or after the loop), so that no step needs
+    // a barrier of its own before its counters are cleared again.
+    const int cstride = 3 * TY + 2;
+    auto write_cell_counts = [&](const int32_t *cb, int64_t czp) {
+        for (int q = tid; q < rows_own + extra; q += nthr) {
+            const int64_t cy = j0 + q - extra;
+            const int64_t rc = (cy + 1) + (ny + 1) * (czp + 1);
+            s.cntP[rc] = cb[TY + q];
+            s.cntS[rc] = cb[2 * TY + 1 + q];
+        }
+    };
+    bool prev_cells = false;
     const int64_t k_step_end = (k0 + tl.kz < nz) ? k0 + tl.kz : nz; // kk == nz: zero planes (cz = nz-1)
     for (int64_t kk = k0; kk <= k_step_end; ++kk) {
         const bool have = kk < k_ld_end;
         const bool have_next = kk + 1 < k_ld_end && kk < k_own_end;
+        int32_t *cb = cnt + (int)((kk - k0) & 1) * cstride;       // this step's counters
+        const int32_t *cbp = cnt + (int)((kk - k0 + 1) & 1) * cstride; // the previous step's
         if (tl.aligned && tid == 0) { // one thread waits; the barrier below releases the others
             for (int d = 0; d < 2; ++d) {
                 const int64_t kq = kk + d;
@@ -224,7 +270,8 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
                 }
             }
         }
-        for (int e = tid; e < 3 * TY + 2; e += nthr) cnt[e] = 0;
+        // (the previous reads of this set ended before the previous step's second barrier)
+        for (int e = tid; e < cstride; e += nthr) cb[e] = 0;
         T *S0w = reinterpret_cast<T *>(slots + (size_t)((kk - k0) % kCountSlots) * tl.slot_bytes);
         T *S1w = reinterpret_cast<T *>(slots + (size_t)((kk + 1 - k0) % kCountSlots) * tl.slot_bytes);
         const T *S0 = S0w, *S1 = S1w;
@@ -239,24 +286,38 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
             if (have_next)
                 for (int64_t e = tid; e < n; e += nthr) S1w[e] = (T)kappa<MODE>(c, (uint32_t)S1w[e]);
         }
+        // first barrier: slices kk and kk+1 have landed, the previous step's cell
+        // pass (plane reads, counter atomics) is complete
         __syncthreads();
-        // ---- Passes 1-2 for slice kk: one thread per (row, word)
-        for (int it = tid; it < (TY + 1) * W; it += nthr) {
+        if (prev_cells) write_cell_counts(cbp, kk - 2);
+        // ---- Passes 1-2 for slice kk: one lane per (row, word); the loop runs
+        // warp-uniformly (the fast compares exchange samples between lanes)
+        for (int it0 = tid - lane; it0 < (TY + 1) * W; it0 += nthr) {
+            const int it = it0 + lane;
+            const bool live = it < (TY + 1) * W;
             const int r = (int)(((uint64_t)(uint32_t)it * tl.wdiv) >> 32), w = it - r * W;
-            uint32_t xw = 0, yw = 0, zw = 0;
-            if (have && r < rows_ld) {
-                const T *row = S0 + (int64_t)r * lp;
-                const bool doY = r < rows_own && r + 1 < rows_ld;
-                // (the fast form compares classes already in shared memory)
-                edge_words<T, FAST ? (int)CLASS_ALL : MODE, FAST>(c, row, row + lp, S1 + (int64_t)r * lp, nx, w, doY,
-                                                                  have_next, xw, yw, zw);
-                if (r < rows_own && (xw | yw | zw)) atomicAdd(&cnt[r], __popc(xw) + __popc(yw) + __popc(zw));
+            const bool in = live && have && r < rows_ld;
+            const T *row = S0 + (int64_t)(in ? r : 0) * lp;
+            const bool doY = r < rows_own && r + 1 < rows_ld;
+            uint32_t xw, yw, zw;
+            // (the fast form compares classes already in shared memory)
+            edge_words<T, FAST ? (int)CLASS_ALL : MODE, FAST>(c, row, row + lp, S1 + (int64_t)(in ? r : 0) * lp, nx,
+                                                              w, W, lane, in, doY, have_next, xw, yw, zw);
+            if (in && r < rows_own && (xw | yw | zw)) atomicAdd(&cb[r], __popc(xw) + __popc(yw) + __popc(zw));
+            if (live) {
+                PL(cur, 0, r)[w] = xw;
+                PL(cur, 1, r)[w] = yw;
+                PL(cur, 2, r)[w] = zw;
             }
-            PL(cur, 0, r)[w] = xw;
-            PL(cur, 1, r)[w] = yw;
-            PL(cur, 2, r)[w] = zw;
         }
+        // second barrier: slice kk's planes and quad counts are complete, and
+        // slice kk's slot is read no more
         __syncthreads();
+        if (have) { // refill the slot with slice kk + kCountSlots
+            const int slot = (int)((kk - k0) % kCountSlots);
+            phase_bits ^= 1u << slot;
+            issue(kk + kCountSlots);
+        }
         // ---- owned sample rows of slice kk: planes and quad counts to global memory
         if (kk < k_own_end) {
             for (int it = tid; it < rows_own * W; it += nthr) {
@@ -266,7 +327,7 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
                 s.Y[rs * g.WS + w] = PL(cur, 1, r)[w];
                 s.Z[rs * g.WS + w] = PL(cur, 2, r)[w];
             }
-            for (int r = tid; r < rows_own; r += nthr) s.cntQ[(j0 + r) + ny * kk] = cnt[r];
+            for (int r = tid; r < rows_own; r += nthr) s.cntQ[(j0 + r) + ny * kk] = cb[r];
         }
         // ---- Pass 3 for cell rows (cy, cz = kk-1): sample rows cy, cy+1 of slices cz (prev) and cz+1 (cur)
         const int64_t cz = kk - 1;
@@ -313,32 +374,18 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
                 const int64_t rc = (cy + 1) + (ny + 1) * (cz + 1);
                 s.P[rc * g.WS + w] = pw;
                 if (pw) {
-                    atomicAdd(&cnt[TY + q], __popc(pw));
-                    atomicAdd(&cnt[2 * TY + 1 + q], deg);
+                    atomicAdd(&cb[TY + q], __popc(pw));
+                    atomicAdd(&cb[2 * TY + 1 + q], deg);
                 }
             }
         }
-        __syncthreads();
-        if (do_cells) {
-            for (int q = tid; q < rows_own + extra; q += nthr) {
-                const int64_t cy = j0 + q - extra;
-                const int64_t rc = (cy + 1) + (ny + 1) * (cz + 1);
-                s.cntP[rc] = cnt[TY + q];
-                s.cntS[rc] = cnt[2 * TY + 1 + q];
-            }
-        }
-        // slice kk's slot is free: refill it with slice kk + kCountSlots
-        if (have) {
-            const int slot = (int)((kk - k0) % kCountSlots);
-            phase_bits ^= 1u << slot;
-            issue(kk + kCountSlots);
-        }
-        __syncthreads(); // the counters are read above and cleared at the top of the next step
-        cur ^= 1;        // the next step overwrites every row of this buffer
+        prev_cells = do_cells;
+        cur ^= 1; // the next step overwrites every row of this buffer (after its first barrier)
     }
     // the planes just written are read by bulk copies (async proxy) of later tiles
     asm volatile("fence.proxy.async.global;" ::: "memory");
     const bool ok = !__syncthreads_or(failed);
+    if (prev_cells) write_cell_counts(cnt + (int)((k_step_end - k0) & 1) * cstride, k_step_end - 1);
     // every copy issued has been waited for: the barriers can be retired so that
     // the shared memory may hold other barriers in a later tile of the same CTA
     if (ok && tid == 0)

@@ -548,7 +548,7 @@ bool count_tiling(int type, const void *labels, const Geometry &g, CountTiling *
     // items of a slice fill the 256 threads as evenly as possible
     int ty = 0;
     double best = -1.0;
-    for (int t = 1; t <= 16; ++t) {
+    for (int t = 1; t <= kCountMaxTY; ++t) {
         if ((t + 1) * row_bytes > kSlotBudget) break;
         const int64_t items = (int64_t)(t + 1) * g.W;
         const double fill = (double)(t * g.W) / (double)(((items + 255) / 256) * 256);

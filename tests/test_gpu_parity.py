@@ -52,6 +52,17 @@ def test_uint8_rows_on_16_byte_boundaries(nx):
     parity(lab, iterations=6)
 
 
+@pytest.mark.parametrize("dtype,nx", [(np.uint16, 72), (np.uint16, 200), (np.uint16, 360), (np.uint32, 68),
+                                      (np.uint32, 164)])
+def test_packed_rows_with_words_not_dividing_a_warp(dtype, nx):
+    """Rows on 16-byte boundaries (the packed counting form) with 3-12 words per row: a warp's lanes span row
+    ends, so the sample after a word comes from the next lane or, for the warp's last lane, from shared memory."""
+    rng = np.random.default_rng(nx)
+    lab = rng.integers(0, 3, size=(6, 9, nx)).astype(dtype)
+    parity(lab, iterations=3)
+    parity(lab, selected=[1], background=0, iterations=2)
+
+
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16, np.uint32])
 def test_ellipsoids_each_dtype(dtype):
     lab = sn_synth.ellipsoids((70, 45, 38), 6, 4.0, 15.0, dtype, seed=9)
