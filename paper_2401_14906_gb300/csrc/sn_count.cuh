@@ -24,10 +24,8 @@ constexpr int kCountHeader = 1024; // mbarriers (24 B) + two sets of row counter
 static_assert(32 + 2 * (3 * kCountMaxTY + 2) * 4 <= kCountHeader, "row counters overflow the header");
 
 // --- edge words of 32 samples from rows in shared memory, packed-integer form.
-// flags16(x): bit 15 / bit 31 set iff the low / high 16-bit half of x is
-// nonzero; flags8(x): bit 7 of each byte set iff that byte is nonzero (the
-// 0x7fff / 0x7f additions cannot carry across halves or bytes).
-__device__ __forceinline__ uint32_t flags16(uint32_t x) { return ((x & 0x7fff7fffu) + 0x7fff7fffu) | x; }
+// flags8(x): bit 7 of each byte set iff that byte is nonzero (the 0x7f
+// additions cannot carry across bytes).
 __device__ __forceinline__ uint32_t flags8(uint32_t x) { return ((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x; }
 // bit 7 of the four bytes of u, packed into bits 0..3
 __device__ __forceinline__ uint32_t nibble(uint32_t u) { return (((u >> 7) & 0x01010101u) * 0x01020408u) >> 24; }
@@ -47,12 +45,27 @@ template <typename T> struct WordChunks {
     __device__ static __forceinline__ int rot(int w) { return (w / LANES) & (C - 1); }
 };
 
-// mask bit e set iff sample e of a xor-ed chunk is nonzero
+// per 16-bit half, the smaller of a and b (one SIMD instruction)
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// mask bit e set iff sample e of a xor-ed chunk is nonzero.  uint16: min(half, 1)
+// leaves each sample's flag in bit 0 of byte 0 or 2 of its word; two byte
+// permutes gather the flags of samples 0-3 into bit 0 and of samples 4-7 into
+// bit 4 of the four bytes of q, and the product with 0x01020408 moves the flag
+// of byte i to bit 24 + i (bit 0) and 28 + i (bit 4) with every other partial
+// product on a distinct lower bit or beyond bit 31, so nothing carries.
 template <typename T> __device__ __forceinline__ uint32_t chunk_bits(uint4 x);
 template <> __device__ __forceinline__ uint32_t chunk_bits<uint16_t>(uint4 x)
 {
-    return nibble(__byte_perm(flags16(x.x), flags16(x.y), 0x7531)) |
-           (nibble(__byte_perm(flags16(x.z), flags16(x.w), 0x7531)) << 4);
+    const uint32_t one = 0x00010001u;
+    const uint32_t q = __byte_perm(min_u16x2(x.x, one), min_u16x2(x.y, one), 0x6420) |
+                       (__byte_perm(min_u16x2(x.z, one), min_u16x2(x.w, one), 0x6420) << 4);
+    return (q * 0x01020408u) >> 24;
 }
 template <> __device__ __forceinline__ uint32_t chunk_bits<uint8_t>(uint4 x)
 {
