@@ -382,12 +382,26 @@ def run_ours(args):
                 return ((ctypes.c_int64 * 3)(*w.dims), (ctypes.c_double * 3)(*w.spacing),
                         (ctypes.c_double * 3)(*w.origin))
 
-            def start(bufs):
-                """upload + extract + smooth of one map, then the asynchronous copy-out into `bufs`"""
+            def upload():
+                """start copying the step's labels to the device (returns at once)"""
+                d, _, _ = c_args()
+                up = ctypes.c_void_p()
+                rc = lib.sn_labels_upload(ctypes.c_void_p(host_lab.data_ptr()), b, d, ctypes.byref(up))
+                assert rc == 0, sn.sn_last_error()
+                return up
+
+            def start(bufs, up=None):
+                """extract + smooth of one map, from its upload or (up None) from host labels copied during the
+                call, then the asynchronous copy-out into `bufs`"""
                 d, sp, org = c_args()
                 out = ctypes.c_void_p()
-                rc = lib.sn_extract(ctypes.c_void_p(host_lab.data_ptr()), b, d, sp, org, None, 0, w.background,
-                                    ctypes.c_void_p(stream.cuda_stream), ctypes.byref(out))
+                st = ctypes.c_void_p(stream.cuda_stream)
+                if up is None:
+                    rc = lib.sn_extract(ctypes.c_void_p(host_lab.data_ptr()), b, d, sp, org, None, 0,
+                                        w.background, st, ctypes.byref(out))
+                else:
+                    rc = lib.sn_extract_labels(up, sp, org, None, 0, w.background, st, ctypes.byref(out))
+                    lib.sn_labels_free(up, st)
                 assert rc == 0, sn.sn_last_error()
                 rc = lib.sn_smooth(out, w.iterations, w.relaxation, w.constraint)
                 assert rc == 0
@@ -403,13 +417,18 @@ def run_ours(args):
                 lib.sn_free(out)
 
             def e2e_run(steps, pipelined):
-                """each step's copy-out overlaps the next step's upload and kernels (two output buffers)"""
+                """one step at a time (host labels copied inside sn_extract), or pipelined: each step's labels
+                are uploaded while the previous step is extracted and smoothed, and its copy-out overlaps
+                the next step (two output buffers)"""
                 prev = None
+                up = upload() if pipelined and steps else None
                 for k in range(steps):
-                    cur = start(out_sets[k % 2])
                     if not pipelined:
-                        finish(cur)
+                        finish(start(out_sets[k % 2]))
                         continue
+                    nxt = upload() if k + 1 < steps else None
+                    cur = start(out_sets[k % 2], up)
+                    up = nxt
                     if prev is not None:
                         finish(prev)
                     prev = cur
@@ -436,9 +455,10 @@ def run_ours(args):
             e2e = {"value": world * V * args.steps / (ems / 1e3) / 1e9, "unit": UNIT,
                    "h2d_bytes_per_step": V * b, "d2h_bytes_per_step": int(d2h),
                    "ms_per_step": ems / args.steps,
-                   "timing": "host clock around K steps; each step uploads its labels from pinned memory, "
-                             "extracts, smooths and copies its mesh back to pinned memory; a step's copy-out "
-                             "overlaps the next step's upload (sn_mesh_copy_to_host_async)",
+                   "timing": "host clock around K steps; each step uploads its labels from pinned memory "
+                             "(sn_labels_upload, issued one step ahead so that it overlaps the previous step), "
+                             "extracts (sn_extract_labels), smooths and copies its mesh back to pinned memory "
+                             "(sn_mesh_copy_to_host_async, overlapping the next step)",
                    "one_step_at_a_time_ms_per_step": e2e_ms[False] / args.steps}
 
     if rank != 0:

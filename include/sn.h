@@ -86,6 +86,41 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
                      void *cuda_stream, sn_mesh **out);
 
 /*
+ * sn_labels_upload / sn_extract_labels / sn_labels_wait / sn_labels_free --
+ * a label map copied to the device ahead of its extraction, so that a caller
+ * processing a sequence of host maps can copy map k+1 while map k is being
+ * extracted and smoothed (sn_extract on host labels copies during the call).
+ *
+ * sn_labels_upload starts copying `host_labels` (dims[0]*dims[1]*dims[2]
+ * values of `type`, x fastest; the same limits as sn_extract) into device
+ * memory owned by the returned handle, and returns at once.  The copy runs on
+ * the library's copy stream of the calling thread, after the copies queued
+ * there before it.  The host memory must stay valid and unchanged until the
+ * copy is complete (sn_labels_wait, or the work of an sn_extract_labels call
+ * on that map); with pageable memory the call returns once the host buffer
+ * has been read (the device side of the copy may still be in flight).
+ * Errors: SN_EINVAL, SN_ENOMEM, SN_ECUDA; *out is NULL on failure.
+ *
+ * sn_extract_labels is sn_extract over the uploaded map: `cuda_stream` first
+ * waits for the copy (a stream dependency, not a host wait), then the call
+ * proceeds exactly as sn_extract with device labels.  The handle may be
+ * extracted any number of times.
+ *
+ * sn_labels_wait blocks until the copy is complete.
+ *
+ * sn_labels_free releases the device copy once the copy and the work already
+ * queued on `cuda_stream` are done (stream-ordered; pass the stream of the
+ * extractions that read it).  NULL is ignored.
+ */
+typedef struct sn_labels sn_labels; /* opaque, owned by the library until sn_labels_free */
+sn_status sn_labels_upload(const void *host_labels, sn_label_type type, const int64_t dims[3], sn_labels **out);
+sn_status sn_extract_labels(const sn_labels *labels, const double spacing[3], const double origin[3],
+                            const uint32_t *selected, int64_t n_selected, uint32_t background, void *cuda_stream,
+                            sn_mesh **out);
+sn_status sn_labels_wait(const sn_labels *labels);
+void sn_labels_free(sn_labels *labels, void *cuda_stream);
+
+/*
  * sn_smooth -- constrained Laplacian smoothing (Sec. 2.2 Eq. 1, Sec. 2.4).
  *
  * Restarts from the cell centres, then runs `iterations` Jacobi sweeps:

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <new>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -33,6 +34,15 @@ struct sn_mesh {
     cudaEvent_t copied;    // the last sn_mesh_copy_to_host_async has finished
     int32_t *copy_meta;    // its copy of the meta words (pinned)
     bool copy_pending;
+};
+
+// A label map copied to the device ahead of its extraction (sn_labels_upload).
+struct sn_labels {
+    int device = 0;
+    sn_label_type type = SN_U8;
+    int64_t dims[3] = {0, 0, 0};
+    void *data = nullptr;           // device copy, from the device's memory pool
+    cudaEvent_t uploaded = nullptr; // recorded on the copy stream after the copy
 };
 
 struct sn_learner {
@@ -671,6 +681,91 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
     }
     job_release(j, st);
     return r;
+}
+
+sn_status sn_labels_upload(const void *host_labels, sn_label_type type, const int64_t dims[3], sn_labels **out)
+{
+    g_last_error.clear();
+    if (!out) return fail(SN_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!host_labels) return fail(SN_EINVAL, "labels is NULL");
+    if (type != SN_U8 && type != SN_U16 && type != SN_U32) return fail(SN_EINVAL, "bad label type");
+    if (!dims) return fail(SN_EINVAL, "dims is NULL");
+    const int64_t kMaxDim = (1ll << 21) - 2;
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 1 || dims[a] > kMaxDim) return fail(SN_EINVAL, "dims must be in [1, 2^21-2]");
+    const int64_t V = dims[0] * dims[1] * dims[2];
+    if (V >= (1ll << 40)) return fail(SN_EINVAL, "nx*ny*nz must be < 2^40");
+    sn_labels *L = new (std::nothrow) sn_labels;
+    if (!L) return fail(SN_ENOMEM, "host allocation of the label handle failed");
+    L->type = type;
+    for (int a = 0; a < 3; ++a) L->dims[a] = dims[a];
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = cudaGetDevice(&L->device);
+    if (e == cudaSuccess) e = device_pool(L->device, &pool);
+    if (e != cudaSuccess) {
+        delete L;
+        return cuda_fail(e, "label upload: device or memory pool");
+    }
+    cudaStream_t cs = copy_stream(L->device);
+    if (!cs) {
+        delete L;
+        return fail(SN_ECUDA, "label upload: the copy stream could not be created");
+    }
+    const size_t bytes = (size_t)V * (size_t)type;
+    sn_status r = pool_alloc(&L->data, bytes, pool, cs, "uploaded labels");
+    if (r != SN_OK) {
+        delete L;
+        return r;
+    }
+    e = cudaMemcpyAsync(L->data, host_labels, bytes, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->uploaded, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(L->uploaded, cs);
+    if (e != cudaSuccess) {
+        r = cuda_fail(e, "label upload");
+        if (L->uploaded) cudaEventDestroy(L->uploaded);
+        pool_free(L->data, cs);
+        delete L;
+        return r;
+    }
+    *out = L;
+    return SN_OK;
+}
+
+sn_status sn_extract_labels(const sn_labels *labels, const double spacing[3], const double origin[3],
+                            const uint32_t *selected, int64_t n_selected, uint32_t background, void *cuda_stream,
+                            sn_mesh **out)
+{
+    g_last_error.clear();
+    if (out) *out = nullptr;
+    if (!labels || !labels->data || !labels->uploaded) return fail(SN_EINVAL, "labels is NULL or not uploaded");
+    cudaError_t e = cudaStreamWaitEvent((cudaStream_t)cuda_stream, labels->uploaded, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "waiting for the label upload");
+    return sn_extract(labels->data, labels->type, labels->dims, spacing, origin, selected, n_selected, background,
+                      cuda_stream, out);
+}
+
+sn_status sn_labels_wait(const sn_labels *labels)
+{
+    g_last_error.clear();
+    if (!labels || !labels->uploaded) return fail(SN_EINVAL, "labels is NULL or not uploaded");
+    cudaError_t e = cudaEventSynchronize(labels->uploaded);
+    if (e != cudaSuccess) return cuda_fail(e, "label upload");
+    return SN_OK;
+}
+
+void sn_labels_free(sn_labels *labels, void *cuda_stream)
+{
+    if (!labels) return;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (labels->data) {
+        // stream-ordered after the copy as well as after the work queued on `st`
+        if (labels->uploaded) cudaStreamWaitEvent(st, labels->uploaded, 0);
+        pool_free(labels->data, st);
+    }
+    if (labels->uploaded) cudaEventDestroy(labels->uploaded);
+    cudaGetLastError();
+    delete labels;
 }
 
 sn_status sn_smooth(sn_mesh *m, int iterations, float relaxation, float constraint_distance)

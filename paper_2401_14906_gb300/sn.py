@@ -40,6 +40,11 @@ _DP = ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "sn_extract": (ctypes.c_int, [_P, ctypes.c_int, _I64P, _DP, _DP, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int64,
                                   ctypes.c_uint32, _P, ctypes.POINTER(_P)]),
+    "sn_labels_upload": (ctypes.c_int, [_P, ctypes.c_int, _I64P, ctypes.POINTER(_P)]),
+    "sn_extract_labels": (ctypes.c_int, [_P, _DP, _DP, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int64,
+                                         ctypes.c_uint32, _P, ctypes.POINTER(_P)]),
+    "sn_labels_wait": (ctypes.c_int, [_P]),
+    "sn_labels_free": (None, [_P, _P]),
     "sn_smooth": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_float, ctypes.c_float]),
     "sn_smooth_ex": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_int]),
     "sn_triangulate": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -198,6 +203,69 @@ def sn_extract(labels, spacing=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0), selected
     del keep, sel_keep
     _check(rc)
     return Mesh(out.value, tcode, dims, spacing, origin)
+
+
+class Labels:
+    """Owner of an sn_labels* (a label map copied to the device ahead of its extraction).  The host
+    array or pinned tensor it was uploaded from is kept alive until free()."""
+
+    def __init__(self, handle, label_type, dims, keep):
+        self._h = ctypes.c_void_p(handle)
+        self.label_type = label_type
+        self.dims = dims
+        self._keep = keep
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("labels have been freed")
+        return self._h
+
+    def wait(self):
+        _check(load().sn_labels_wait(self.handle))
+
+    def free(self, stream=None):
+        """Stream-ordered release: after the copy and the work already queued on `stream`
+        (default: torch's current stream)."""
+        if self._h:
+            load().sn_labels_free(self._h, ctypes.c_void_p(_stream_handle(stream, True)))
+            self._h = ctypes.c_void_p(None)
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sn_labels_upload(labels) -> Labels:
+    """Start copying a host (nz, ny, nx) label map (numpy array, or a pinned CPU tensor for an
+    asynchronous copy) to the device; returns at once."""
+    ptr, tcode, dims, is_cuda, keep = _label_info(labels)
+    if is_cuda:
+        raise ValueError("sn_labels_upload takes host labels; pass device labels to sn_extract directly")
+    out = ctypes.c_void_p()
+    _check(load().sn_labels_upload(ctypes.c_void_p(ptr), tcode, (ctypes.c_int64 * 3)(*dims), ctypes.byref(out)))
+    return Labels(out.value, tcode, dims, keep)
+
+
+def sn_extract_labels(labels: Labels, spacing=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0), selected=None, background=0,
+                      stream=None) -> Mesh:
+    """sn_extract over an uploaded map; the stream waits for the upload on the device."""
+    sp = (ctypes.c_double * 3)(*[float(s) for s in spacing])
+    org = (ctypes.c_double * 3)(*[float(o) for o in origin])
+    sel_ptr, nsel, sel_keep = None, 0, None
+    if selected is not None:
+        sel_keep = np.ascontiguousarray(np.asarray(selected, dtype=np.uint32))
+        sel_ptr = sel_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+        nsel = int(sel_keep.size)
+    out = ctypes.c_void_p()
+    rc = load().sn_extract_labels(labels.handle, sp, org, sel_ptr, nsel, int(background),
+                                  ctypes.c_void_p(_stream_handle(stream, True)), ctypes.byref(out))
+    del sel_keep
+    _check(rc)
+    return Mesh(out.value, labels.label_type, labels.dims, spacing, origin)
 
 
 SN_CONSTRAINT_BOX, SN_CONSTRAINT_SPHERE = 0, 1

@@ -19,14 +19,19 @@ def run_gpu(labels, spacing=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0), selected=No
     import torch
 
     from paper_2401_14906_gb300 import sn
-    if on_device:
+    if on_device == "uploaded":  # copied ahead by sn_labels_upload, then sn_extract_labels
+        up = sn.sn_labels_upload(np.ascontiguousarray(labels))
+        m = sn.sn_extract_labels(up, spacing, origin, selected=selected, background=background)
+        up.free()
+    elif on_device:
         t = torch.from_numpy(np.ascontiguousarray(labels).view(
             {1: np.uint8, 2: np.int16, 4: np.int32}[labels.dtype.itemsize])).cuda()
         t = t.view({1: torch.uint8, 2: torch.uint16, 4: torch.uint32}[labels.dtype.itemsize])
         src = t
     else:
         src = np.ascontiguousarray(labels)
-    m = sn.sn_extract(src, spacing, origin, selected=selected, background=background)
+    if on_device != "uploaded":
+        m = sn.sn_extract(src, spacing, origin, selected=selected, background=background)
     ext = sn.sn_mesh_copy_to_host(m)
     ext["face_masks"] = sn.sn_mesh_face_masks_host(m)
     smo = None

@@ -87,6 +87,34 @@ def test_smooth_and_accessor_validation(lib):
     lib.sn_free(None)
 
 
+def test_label_upload_validation(lib):
+    """Argument errors of the upload calls are reported before any CUDA call."""
+    from paper_2401_14906_gb300 import sn
+    E = sn.SN_EINVAL
+    arr = np.zeros(64, np.uint16)
+
+    def up(ptr=True, type_=2, dims=(4, 4, 4), out=True):
+        o = ctypes.c_void_p(123)
+        rc = lib.sn_labels_upload(ctypes.c_void_p(arr.ctypes.data if ptr else 0), type_,
+                                  (ctypes.c_int64 * 3)(*dims), ctypes.byref(o) if out else None)
+        if out:
+            assert o.value is None  # cleared on failure
+        return rc
+    assert up(ptr=False) == E
+    assert up(type_=3) == E
+    assert up(dims=(0, 4, 4)) == E
+    assert up(dims=(4, 4, 1 << 22)) == E
+    assert up(dims=(1 << 20, 1 << 20, 2)) == E  # 2^41 samples
+    assert up(out=False) == E
+    one = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    zero = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    o = ctypes.c_void_p(123)
+    assert lib.sn_extract_labels(None, one, zero, None, 0, 0, None, ctypes.byref(o)) == E
+    assert o.value is None
+    assert lib.sn_labels_wait(None) == E
+    lib.sn_labels_free(None, None)
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     from paper_2401_14906_gb300 import sn
     with pytest.raises(RuntimeError, match="libsn.so not found"):

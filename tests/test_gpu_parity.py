@@ -64,6 +64,35 @@ def test_packed_rows_with_words_not_dividing_a_warp(dtype, nx):
 
 
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16, np.uint32])
+def test_uploaded_labels(dtype):
+    """Labels copied ahead by sn_labels_upload, then extracted by sn_extract_labels."""
+    lab = sn_synth.ellipsoids((45, 38, 30), 5, 4.0, 13.0, dtype, seed=21)
+    parity(lab, iterations=6, on_device="uploaded")
+    parity(lab, selected=[1, 3], background=0, iterations=3, on_device="uploaded")
+
+
+def test_uploads_ahead_of_extraction_match_direct_calls():
+    """Three pinned maps uploaded before any extraction, one of them extracted twice, all freed in stream
+    order: each mesh equals the one sn_extract gives for the same map."""
+    import torch
+    from paper_2401_14906_gb300 import sn
+    maps = [sn_synth.ellipsoids((64, 48, 40), 6, 4.0, 14.0, np.uint16, seed=30 + k) for k in range(3)]
+    pinned = [torch.from_numpy(m.view(np.int16)).pin_memory().view(torch.uint16) for m in maps]
+    ups = [sn.sn_labels_upload(p) for p in pinned]
+    for k in (0, 1, 2, 1):
+        m, ref = sn.sn_extract_labels(ups[k]), sn.sn_extract(maps[k])
+        a, b = sn.sn_mesh_copy_to_host(m), sn.sn_mesh_copy_to_host(ref)
+        assert a["points"].shape[0] > 100
+        for key in a:
+            np.testing.assert_array_equal(a[key], b[key])
+        m.free()
+        ref.free()
+    ups[2].wait()
+    for u in ups:
+        u.free()
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16, np.uint32])
 def test_ellipsoids_each_dtype(dtype):
     lab = sn_synth.ellipsoids((70, 45, 38), 6, 4.0, 15.0, dtype, seed=9)
     parity(lab, iterations=16)
