@@ -1,6 +1,6 @@
 // sn_count.cuh -- Passes 1-3 of the extraction as one streaming tile (Sec. 2.2-2.3,
-// 3.1-3.4); used by the single-map counting kernel (sn_extract.cu) and by the
-// batched kernel (sn_batch.cu).
+// 3.1-3.4); the body of k_count (sn_extract.cu), which the batched extraction
+// also launches, once per map.
 #pragma once
 
 #include "sn_device.cuh"
@@ -13,8 +13,8 @@ namespace dev {
 // (k0..k0+KZ-1).  It streams the slices through shared memory -- each slice's
 // TY+1 rows (one halo row) are one contiguous block of the label map, copied by
 // the TMA engine (cp.async.bulk, three-slot ring, one mbarrier per slot) -- and
-// for every slice builds the X/Y/Z words of its rows with warp ballots (Passes
-// 1-2), writes those of the rows it owns, and combines the planes of slices
+// for every slice builds the X/Y/Z words of its rows by packed compares of
+// 16-byte chunks (Passes 1-2), writes those of the rows it owns, and combines the planes of slices
 // cz and cz+1 (kept in shared memory) into the face and point planes of cell
 // rows (cy, cz) with their point and stencil counts (Pass 3).  Every label is
 // read from HBM once; halo rows and the halo slice come from L2.
@@ -195,8 +195,7 @@ __device__ __forceinline__ void edge_words(const Classifier &c, const T *row, co
     }
 }
 
-// One tile (bx, by) of the counting pass; called by the single-map and the
-// batched kernels.  Label rows are g.lp elements apart.  Returns false (in every
+// One tile (bx, by) of the counting pass.  Label rows are g.lp elements apart.  Returns false (in every
 // thread) when a label copy wait gave up; the copy may then still be in flight.
 template <typename T, int MODE, bool FAST>
 __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Classifier &c, const Geometry &g,

@@ -1,6 +1,6 @@
 // sn_emit_tile.cuh -- Pass 4 of the extraction (Sec. 2.3 "Generate output", Sec.
-// 3.6) over a tile of cell rows; used by the single-map kernel (sn_emit.cu) and
-// by the batched kernel (sn_batch.cu).
+// 3.6) over a tile of cell rows; the body of k_emit_tile (sn_emit.cu), which the
+// batched extraction also launches, once per map.
 #pragma once
 
 #include "sn_device.cuh"
@@ -43,12 +43,11 @@ __device__ __forceinline__ int nth_bit(uint32_t word, int nth)
     return b;
 }
 
-// One tile (bx = run of cell rows, by = cz + 1) of the emission; called by the
-// single-map and the batched kernels.  Label rows are g.lp elements apart.
-// Counts, offsets and totals are read through L2 and the bit planes by bulk
-// copies after a proxy fence: in the batched kernel other CTAs of the same
-// launch wrote them.  Returns false (in every thread) when the staging wait
-// gave up; the copies may then still be in flight.
+// One tile (bx = run of cell rows, by = cz + 1) of the emission.  Label rows
+// are g.lp elements apart.  Counts, offsets and totals are read through L2, and
+// the bit planes (written by ordinary stores of the counting pass) by bulk
+// copies after a proxy fence.  Returns false (in every thread) when the staging
+// wait gave up; the copies may then still be in flight.
 template <typename T, int MODE>
 __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Classifier &c, const Geometry &g,
                                           const ExtractScratch &s, const MeshArrays &m, DevTotals *tot,

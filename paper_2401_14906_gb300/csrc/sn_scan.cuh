@@ -1,6 +1,5 @@
 // sn_scan.cuh -- the row prefix sum of Pass 3 (Sec. 2.3, 3.5): decoupled look-back
-// over tiles of cell rows; used by the single-map scan (sn_extract.cu) and by the
-// batched kernel (sn_batch.cu).
+// over tiles of cell rows; the body of k_scan (sn_extract.cu).
 #pragma once
 
 #include "sn_device.cuh"

@@ -1,6 +1,6 @@
 // sn_sweep.cuh -- one Jacobi sweep of the constrained smoothing (Sec. 2.2 Eq. 1,
-// Sec. 2.4) over a block of points; used by the single-map kernel (sn_smooth.cu)
-// and by the batched kernel (sn_batch.cu).
+// Sec. 2.4) over a block of points; used by the single-map sweep k_smooth and
+// by the batched sweep k_smooth_batch (both in sn_smooth.cu).
 //
 // Positions are FP32 offsets o from the generating cell centre, in voxel
 // units.  For face neighbours p_j - p_i = u_ij + (o_j - o_i), with u_ij the unit
