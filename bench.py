@@ -191,6 +191,44 @@ def traffic_for(kernel):
         return None
 
 
+def host_link_floor(h2d_bytes, d2h_bytes, reps=5):
+    """The step's copies alone, pinned host <-> device (torch copies on two streams): H2D only, D2H only, and
+    both at once -- the floor under the end-to-end step.  Never raises: a failure is reported in the result."""
+    import torch
+    try:
+        h_in = torch.empty(h2d_bytes, dtype=torch.uint8, pin_memory=True)
+        d_in = torch.empty(h2d_bytes, dtype=torch.uint8, device="cuda")
+        d_out = torch.empty(d2h_bytes, dtype=torch.uint8, device="cuda")
+        h_out = torch.empty(d2h_bytes, dtype=torch.uint8, pin_memory=True)
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+        def h2d():
+            with torch.cuda.stream(s_in):
+                d_in.copy_(h_in, non_blocking=True)
+
+        def d2h():
+            with torch.cuda.stream(s_out):
+                h_out.copy_(d_out, non_blocking=True)
+
+        def both():
+            h2d()
+            d2h()
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fn()
+            torch.cuda.synchronize()
+            return (time.perf_counter() - t0) / reps * 1e3
+        a, b, c = timed(h2d), timed(d2h), timed(both)
+        return {"h2d_ms": a, "h2d_gbs": h2d_bytes / a / 1e6, "d2h_ms": b, "d2h_gbs": d2h_bytes / b / 1e6,
+                "both_ms": c, "timing": "host clock, pinned buffers, the two directions on two streams"}
+    except Exception as e:  # the measurement is context for e2e; it must not cost the bench line
+        return {"error": str(e)}
+
+
 # ---------------------------------------------------------------- reference
 def run_reference(args):
     rank, world, _ = dist_env()
@@ -459,7 +497,8 @@ def run_ours(args):
                              "(sn_labels_upload, issued one step ahead so that it overlaps the previous step), "
                              "extracts (sn_extract_labels), smooths and copies its mesh back to pinned memory "
                              "(sn_mesh_copy_to_host_async, overlapping the next step)",
-                   "one_step_at_a_time_ms_per_step": e2e_ms[False] / args.steps}
+                   "one_step_at_a_time_ms_per_step": e2e_ms[False] / args.steps,
+                   "host_link": host_link_floor(V * b, int(d2h))}
 
     if rank != 0:
         if world > 1:
