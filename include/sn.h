@@ -104,7 +104,8 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
  * sn_extract_labels is sn_extract over the uploaded map: `cuda_stream` first
  * waits for the copy (a stream dependency, not a host wait), then the call
  * proceeds exactly as sn_extract with device labels.  The handle may be
- * extracted any number of times.
+ * extracted any number of times, on the device current at its upload
+ * (another device: SN_EINVAL).
  *
  * sn_labels_wait blocks until the copy is complete.
  *

@@ -739,7 +739,11 @@ sn_status sn_extract_labels(const sn_labels *labels, const double spacing[3], co
     g_last_error.clear();
     if (out) *out = nullptr;
     if (!labels || !labels->data || !labels->uploaded) return fail(SN_EINVAL, "labels is NULL or not uploaded");
-    cudaError_t e = cudaStreamWaitEvent((cudaStream_t)cuda_stream, labels->uploaded, 0);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != labels->device) return fail(SN_EINVAL, "labels were uploaded on another device");
+    e = cudaStreamWaitEvent((cudaStream_t)cuda_stream, labels->uploaded, 0);
     if (e != cudaSuccess) return cuda_fail(e, "waiting for the label upload");
     return sn_extract(labels->data, labels->type, labels->dims, spacing, origin, selected, n_selected, background,
                       cuda_stream, out);
