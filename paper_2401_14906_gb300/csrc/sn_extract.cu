@@ -439,9 +439,8 @@ template <typename T, int MODE>
 cudaError_t count_t(const void *labels, const Classifier &c, const Geometry &g, const ExtractScratch &s,
                     const CountTiling &tl, size_t smem, DevTotals *tot, cudaStream_t st)
 {
-    // packed compares need rows on 16-byte boundaries (labels are classified in shared memory first);
-    // uint8 maps keep the per-sample form: the packed uint8 form is not validated on the GPU
-    if (tl.aligned && sizeof(T) > 1) return count_f<T, MODE, true>(labels, c, g, s, tl, smem, tot, st);
+    // packed compares need rows on 16-byte boundaries (labels are classified in shared memory first)
+    if (tl.aligned) return count_f<T, MODE, true>(labels, c, g, s, tl, smem, tot, st);
     return count_f<T, MODE, false>(labels, c, g, s, tl, smem, tot, st);
 }
 

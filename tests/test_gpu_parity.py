@@ -47,13 +47,13 @@ def test_random_maps(dtype, seed):
 
 @pytest.mark.parametrize("nx", [16, 48, 64, 128])
 def test_uint8_rows_on_16_byte_boundaries(nx):
-    """uint8 maps whose rows are 16-byte aligned take the per-sample counting form."""
+    """uint8 maps whose rows are 16-byte aligned take the packed counting form."""
     lab = sn_synth.ellipsoids((nx, 37, 29), 5, 3.0, 11.0, np.uint8, seed=nx)
     parity(lab, iterations=6)
 
 
-@pytest.mark.parametrize("dtype,nx", [(np.uint16, 72), (np.uint16, 200), (np.uint16, 360), (np.uint32, 68),
-                                      (np.uint32, 164)])
+@pytest.mark.parametrize("dtype,nx", [(np.uint8, 80), (np.uint8, 208), (np.uint16, 72), (np.uint16, 200),
+                                      (np.uint16, 360), (np.uint32, 68), (np.uint32, 164)])
 def test_packed_rows_with_words_not_dividing_a_warp(dtype, nx):
     """Rows on 16-byte boundaries (the packed counting form) with 3-12 words per row: a warp's lanes span row
     ends, so the sample after a word comes from the next lane or, for the warp's last lane, from shared memory."""
