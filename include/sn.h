@@ -157,8 +157,14 @@ sn_status sn_smooth(sn_mesh *m, int iterations, float relaxation, float constrai
  * library until the process exits.  n_points above SN_STATIC_MAX_POINTS is
  * rejected with SN_EINVAL.  The first call on each device looks up the array's
  * device address (cudaGetSymbolAddress, with that device current); make that
- * first call before any stream capture.  Every call shares the array and it
- * keeps the last call's contents (each call clears what it reads first).
+ * first call before any stream capture.  That address is kept for the life of
+ * the process, so do not call this function after cudaDeviceReset (or any other
+ * teardown of the device's primary context) in the same process.  Every call
+ * shares the array and it keeps the last call's contents (each call clears what
+ * it reads first).  A point's stencil is the CSR range [stencil_offsets[i],
+ * stencil_offsets[i+1]) (at most 6 entries are read); its face mask gives the
+ * unit step towards each neighbour and must list the same faces in the same
+ * order, as the masks of sn_mesh_face_masks do.
  * Calls whose GPU work overlaps -- on different streams or from different host
  * threads -- race on the array: issue them in order on one stream.  Errors:
  * SN_EINVAL, SN_ECUDA; sn_last_error() has the detail.
@@ -169,9 +175,9 @@ sn_status sn_smooth_static(const int64_t *stencil_offsets, const int32_t *stenci
                            float *offsets, void *cuda_stream);
 
 /*
- * sn_smooth_ex -- sn_smooth with a choice of constraint (Sec. 2.2: the motion of
- * a point is constrained "as a fraction of the hexahedral voxel cell, or more
- * simply as a constraint sphere centered at the voxel center point").
+ * sn_smooth_ex -- sn_smooth with a choice of constraint.  Sec. 2.2 allows either
+ * a box (a fraction of the voxel cell) or a sphere about the cell centre as the
+ * region a point may not leave.
  *   SN_CONSTRAINT_BOX     |o_a| <= d/2 per axis (what sn_smooth does);
  *   SN_CONSTRAINT_SPHERE  |o| <= d/2, o measured in voxel units (a ball around
  *                         the cell centre; an ellipsoid in world units when the

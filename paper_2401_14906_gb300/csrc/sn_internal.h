@@ -41,7 +41,7 @@ struct Geometry {
     int64_t WS; // row stride in words (W rounded up to a multiple of 4)
     int64_t Rs; // sample rows ny*nz
     int64_t Rc; // cell rows (ny+1)*(nz+1)
-    int64_t lp; // label row pitch in elements (nx for a caller's map; padded in the batched mode)
+    int64_t lp; // label row pitch in elements (always nx: the kernels read the caller's map in place)
 };
 
 // Device temporaries of one extraction.

@@ -40,7 +40,10 @@ __global__ void __launch_bounds__(256) k_smooth_static(const float *__restrict__
     if (i >= np) return;
     const uint32_t m = fmask[i];
     const int64_t b = soff[i];
-    const int n = __popc(m);
+    // the stencil length comes from the CSR range, so that a mask that disagrees
+    // with the offsets never makes the loop read outside point i's entries
+    const int64_t len = soff[i + 1] - b;
+    const int n = len < 0 ? 0 : (len > 6 ? 6 : (int)len);
     const float ox = oin[3 * i + 0], oy = oin[3 * i + 1], oz = oin[3 * i + 2];
     float sx = (float)((int)((m >> 1) & 1u) - (int)(m & 1u));
     float sy = (float)((int)((m >> 3) & 1u) - (int)((m >> 2) & 1u));
@@ -71,7 +74,9 @@ sn_status err(sn_status s, const char *msg)
 }
 
 // Device address of the static array on the current device, looked up once
-// per device (with that device current).
+// per device (with that device current) and kept for the life of the process:
+// after cudaDeviceReset the module is loaded again and this address is stale,
+// which the header states as a limit of the entry point.
 sn_status scratch_address(float **out)
 {
     int dev = 0;

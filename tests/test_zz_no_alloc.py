@@ -6,13 +6,14 @@ start-up, plugins inside an application that owns the GPU's memory).  This
 entry point keeps its ping-pong buffer in a fixed array inside the library.
 These tests call it through the C ABI twice in a row -- on two different meshes
 with different parameters, so the second call runs on whatever the first left in
-the shared array -- and compare each result with sn_smooth's, within the
-offset tolerance of the other parity tests.  The file is named so that pytest
-collects it last.
+the shared array -- and compare each result with sn_smooth's and with the FP64
+oracle's, within the offset tolerance of the other parity tests.  The file is
+named so that pytest collects it last.
 """
 import numpy as np
 import pytest
 
+import oracle
 import sn_synth
 from gpu_util import OFFSET_TOL
 
@@ -49,10 +50,12 @@ def test_two_calls_in_a_row_match_sn_smooth(sn):
     prepared = []
     for lab, it, lam, d in cases:
         m, ref = _mesh_and_reference(sn, lab, it, lam, d)
-        prepared.append((m, ref, it, lam, d))
+        want, _ = oracle.smooth(oracle.extract(lab), iterations=it, relaxation=lam, constraint=d)
+        assert want.shape == ref.shape
+        prepared.append((m, ref, want, it, lam, d))
     assert prepared[1][1].shape[0] < prepared[0][1].shape[0]  # second call leaves stale data in the array
     stream = torch.cuda.current_stream()
-    for m, ref, it, lam, d in prepared:
+    for m, ref, want, it, lam, d in prepared:
         arrs = sn.sn_mesh_device_arrays(m)
         n = int(ref.shape[0])
         assert 0 < n <= sn.SN_STATIC_MAX_POINTS
@@ -62,6 +65,7 @@ def test_two_calls_in_a_row_match_sn_smooth(sn):
         got = out.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert np.abs(got.astype(np.float64) - ref.astype(np.float64)).max() <= OFFSET_TOL
+        assert np.abs(got.astype(np.float64) - want).max() <= OFFSET_TOL
     for m, *_ in prepared:
         m.free()
 
