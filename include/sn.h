@@ -350,6 +350,14 @@ sn_status sn_mesh_face_masks(const sn_mesh *m, const uint8_t **face_masks);
  * dual cells of Sec. 2.2); point ids are ordered by (cz, cy, cx). */
 sn_status sn_mesh_cells(const sn_mesh *m, const uint64_t **cells);
 
+/* Bytes per point of the neighbour record the smoothing sweeps stream (Sec. 2.4
+ * iterations read every point's stencil once per sweep): 8 while every
+ * -y/+y/-z/+z id distance of the mesh is below 2^15, 12 when the -z/+z
+ * distances need 32 bits (slices of more than ~16k points), 0 when the sweeps
+ * read the CSR stencil instead (cell rows of more than ~16k points).  Chosen at
+ * extraction from bounds the row scan computes. */
+sn_status sn_mesh_record_bytes(const sn_mesh *m, int *bytes_per_point);
+
 /* Copies the arrays above into caller-allocated host buffers (any may be NULL)
  * with the layouts of sn_mesh_device_arrays; waits for the mesh's stream.
  * Returns SN_ETIMEOUT if a smoothing launch gave up a bounded wait. */
@@ -393,6 +401,32 @@ typedef struct {
 
 void sn_profile_enable(int on);
 int sn_profile_read(sn_kernel_time *out, int cap, int reset);
+
+/*
+ * Failure injection for tests.  The paper has no counterpart (its Sec. 4 notes
+ * that the full connectome exhausts memory; these calls make the library's own
+ * failure paths fire on demand, with no GPU fault).  Each setting is
+ * process-wide, applies to calls made after it, and stays until changed or
+ * until sn_debug_reset().
+ *
+ * sn_debug_set_spin_limit(n): the row scan's look-back (Pass 3 prefix sum) gives
+ *     up after n further polls of a predecessor that has not published its sums
+ *     (n = 0: one read; n < 0: it gives up at once, so every extraction with more
+ *     than one scan tile, i.e. more than 2048 cell rows, fails).  A wait that
+ *     gives up makes sn_extract return SN_ETIMEOUT before any output is
+ *     allocated or written.  Default 2^22.
+ * sn_debug_fail_allocation(k): the k-th library allocation from now (k = 0: the
+ *     next one; host or device) fails as if memory were exhausted, so the call
+ *     making it returns SN_ENOMEM after releasing what it holds; k < 0: off.
+ *     One-shot: later allocations succeed.
+ * sn_debug_set_point_limit(n): an extraction whose mesh would have more than n
+ *     points returns SN_EOVERFLOW (as one beyond INT32_MAX points does) before
+ *     allocating its outputs; n < 0 restores INT32_MAX.
+ */
+void sn_debug_set_spin_limit(int n);
+void sn_debug_fail_allocation(int64_t k);
+void sn_debug_set_point_limit(int64_t n);
+void sn_debug_reset(void);
 
 #ifdef __cplusplus
 }

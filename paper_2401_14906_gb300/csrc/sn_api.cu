@@ -73,6 +73,24 @@ sn_status cuda_fail(cudaError_t e, const char *where)
     return fail(SN_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// ------------------------------------------------------- failure injection
+// Set only through the sn_debug_* entry points, so that tests can make the
+// library's failure paths fire without faulting a GPU: a look-back wait that
+// gives up, an allocation that fails, a mesh larger than a given point limit.
+std::atomic<int> g_spin_limit{sn::kSpinLimit};
+std::atomic<int64_t> g_alloc_countdown{-1}; // < 0: off; else the allocation that finds it at 0 fails
+std::atomic<int64_t> g_point_limit{INT32_MAX};
+
+// true when this allocation is to fail (the countdown then stays at -1)
+bool injected_alloc_failure()
+{
+    int64_t c = g_alloc_countdown.load();
+    while (c >= 0) {
+        if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) return c == 0;
+    }
+    return false;
+}
+
 // ------------------------------------------------------------- memory pool
 std::mutex g_pool_mu;
 std::map<int, cudaMemPool_t> g_pools;
@@ -107,6 +125,9 @@ sn_status pool_alloc(void **p, size_t bytes, cudaMemPool_t pool, cudaStream_t st
 {
     *p = nullptr;
     size_t n = bytes < 256 ? 256 : bytes;
+    if (injected_alloc_failure())
+        return fail(SN_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) + " bytes for " + what +
+                                   " failed: injected by sn_debug_fail_allocation");
     cudaError_t e = cudaMallocFromPoolAsync(p, n, pool, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -152,6 +173,8 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 namespace sn {
 
 void set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
+int scan_spin_limit() { return g_spin_limit.load(); }
 
 ProfScope::ProfScope(const char *name, cudaStream_t st) : name_(name), st_(st), a_(nullptr), b_(nullptr), on_(false)
 {
@@ -242,7 +265,7 @@ void scratch_items(ExtractJob &j, std::vector<ScratchItem> &zero, std::vector<Sc
     zero = {
         {(void **)&s.cntQ, sizeof(int32_t) * (size_t)g.Rc},
         {(void **)&s.scan_flags, sizeof(int32_t) * (size_t)ntiles},
-        {(void **)&s.scan_ticket, sizeof(uint32_t)},
+        {(void **)&s.scan_ticket, 2 * sizeof(uint32_t)},
     };
     rest = {
         {(void **)&s.X, sizeof(uint32_t) * (size_t)(g.Rs * g.WS)},
@@ -504,7 +527,9 @@ sn_status job_allocate(ExtractJob &j, cudaStream_t st, bool with_smooth_buffer =
                     (htot->error & 1) ? "row scan look-back wait limit reached" : "label copy wait limit reached");
     const int64_t np = htot->n_points, nq = htot->n_quads, ns = htot->n_stencil;
     if (np > (int64_t)INT32_MAX) return fail(SN_EOVERFLOW, "more than INT32_MAX points");
-    sn_mesh *m = (sn_mesh *)std::calloc(1, sizeof(sn_mesh));
+    if (np > g_point_limit.load())
+        return fail(SN_EOVERFLOW, "more points than the limit set by sn_debug_set_point_limit");
+    sn_mesh *m = injected_alloc_failure() ? nullptr : (sn_mesh *)std::calloc(1, sizeof(sn_mesh));
     if (!m) return fail(SN_ENOMEM, "host allocation failed");
     m->device = j.dev;
     m->stream = st;
@@ -518,6 +543,7 @@ sn_status job_allocate(ExtractJob &j, cudaStream_t st, bool with_smooth_buffer =
     m->np = np;
     m->nq = nq;
     m->ns = ns;
+    m->a.rec = sn::rec_mode(*htot);
     const int64_t nx = j.dims[0], ny = j.dims[1], nz = j.dims[2];
     struct {
         void **p;
@@ -534,6 +560,7 @@ sn_status job_allocate(ExtractJob &j, cudaStream_t st, bool with_smooth_buffer =
         {(void **)&m->a.face_mask, (size_t)np, "face masks"},
         {(void **)&m->a.meta, sizeof(int32_t) * 4, "mesh meta"},
         {(void **)&m->a.nbr, sizeof(uint2) * (size_t)np, "smoothing neighbours"},
+        {(void **)&m->a.nbrp, m->a.rec == sn::REC_WIDE ? sizeof(uint32_t) * (size_t)np : 0, "smoothing neighbours"},
         {(void **)&m->a.lut_x, sizeof(float2) * (size_t)(nx + ny + nz + 3), "cell-centre tables"},
     };
     // one block for all outputs (+ the smoothing buffer when asked), each array on a 256-byte boundary
@@ -552,6 +579,7 @@ sn_status job_allocate(ExtractJob &j, cudaStream_t st, bool with_smooth_buffer =
         block += (pl.bytes + 255) / 256 * 256;
     }
     if (smooth_bytes) m->smooth_scratch = reinterpret_cast<float *>(block);
+    if (m->a.rec != sn::REC_WIDE) m->a.nbrp = nullptr; // (given no bytes above)
     m->a.lut_y = m->a.lut_x + (nx + 1);
     m->a.lut_z = m->a.lut_y + (ny + 1);
     j.mesh = m;
@@ -603,6 +631,19 @@ void job_release(ExtractJob &j, cudaStream_t st)
 extern "C" {
 
 void sn_profile_enable(int on) { g_prof_on.store(on ? 1 : 0); }
+
+void sn_debug_set_spin_limit(int limit) { g_spin_limit.store(limit); }
+
+void sn_debug_fail_allocation(int64_t countdown) { g_alloc_countdown.store(countdown < 0 ? -1 : countdown); }
+
+void sn_debug_set_point_limit(int64_t limit) { g_point_limit.store(limit < 0 ? (int64_t)INT32_MAX : limit); }
+
+void sn_debug_reset(void)
+{
+    g_spin_limit.store(sn::kSpinLimit);
+    g_alloc_countdown.store(-1);
+    g_point_limit.store(INT32_MAX);
+}
 
 int sn_profile_read(sn_kernel_time *out, int cap, int reset)
 {
@@ -696,7 +737,7 @@ sn_status sn_labels_upload(const void *host_labels, sn_label_type type, const in
         if (dims[a] < 1 || dims[a] > kMaxDim) return fail(SN_EINVAL, "dims must be in [1, 2^21-2]");
     const int64_t V = dims[0] * dims[1] * dims[2];
     if (V >= (1ll << 40)) return fail(SN_EINVAL, "nx*ny*nz must be < 2^40");
-    sn_labels *L = new (std::nothrow) sn_labels;
+    sn_labels *L = injected_alloc_failure() ? nullptr : new (std::nothrow) sn_labels;
     if (!L) return fail(SN_ENOMEM, "host allocation of the label handle failed");
     L->type = type;
     for (int a = 0; a < 3; ++a) L->dims[a] = dims[a];
@@ -859,6 +900,13 @@ sn_status sn_mesh_cells(const sn_mesh *m, const uint64_t **cells)
     return SN_OK;
 }
 
+sn_status sn_mesh_record_bytes(const sn_mesh *m, int *bytes_per_point)
+{
+    if (!m || !bytes_per_point) return fail(SN_EINVAL, "mesh or output is NULL");
+    *bytes_per_point = m->a.rec == sn::REC_COMPACT ? 8 : m->a.rec == sn::REC_WIDE ? 12 : 0;
+    return SN_OK;
+}
+
 sn_status sn_mesh_copy_to_host(const sn_mesh *m, float *points, int32_t *quads, void *quad_labels,
                                int64_t *stencil_offsets, int32_t *stencil_ids, float *offsets)
 {
@@ -1001,9 +1049,9 @@ void sn_free(sn_mesh *m)
     if (!m) return;
     // device memory goes back to the pool only after copies still running from it
     if (m->copied && cudaStreamWaitEvent(m->stream, m->copied, 0) != cudaSuccess) cudaGetLastError();
-    void *ps[] = {m->a.points,    m->a.offsets, m->a.cells, m->a.quads, m->a.quad_labels, m->a.sten_off,
-                  m->a.sten_ids,  m->a.face_mask, m->a.meta,  m->a.nbr,   m->a.lut_x,       m->smooth_scratch,
-                  m->tris};
+    void *ps[] = {m->a.points,    m->a.offsets,   m->a.cells, m->a.quads, m->a.quad_labels, m->a.sten_off,
+                  m->a.sten_ids,  m->a.face_mask, m->a.meta,  m->a.nbr,   m->a.nbrp,        m->a.lut_x,
+                  m->smooth_scratch, m->tris};
     for (void *p : ps) {
         const char *c = static_cast<const char *>(p);
         if (m->arena && c >= m->arena && c < m->arena + m->arena_bytes) continue; // part of the arena
@@ -1053,7 +1101,7 @@ sn_status sn_learner_create(void *cuda_stream, sn_learner **out)
     g_last_error.clear();
     if (!out) return fail(SN_EINVAL, "output is NULL");
     *out = nullptr;
-    sn_learner *l = (sn_learner *)std::calloc(1, sizeof(sn_learner));
+    sn_learner *l = injected_alloc_failure() ? nullptr : (sn_learner *)std::calloc(1, sizeof(sn_learner));
     if (!l) return fail(SN_ENOMEM, "host allocation failed");
     l->stream = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaGetDevice(&l->device);

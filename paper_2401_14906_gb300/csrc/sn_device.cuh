@@ -80,6 +80,21 @@ __device__ __forceinline__ int64_t sample_row(const Geometry &g, int64_t y, int6
 
 __device__ __forceinline__ uint32_t shl1(uint32_t cur, uint32_t prev) { return (cur << 1) | (prev >> 31); }
 
+// The sweeps' neighbour record of point id (face mask, |id distance| to the
+// -y/+y/-z/+z neighbours, 0 = absent) in the mesh's record mode; the reach
+// bounds that chose the mode guarantee that the distances fit its fields.
+__device__ __forceinline__ void store_record(const MeshArrays &m, int32_t id, uint32_t mask, const uint32_t (&d)[4])
+{
+    if (m.rec == REC_CSR) return;
+    const uint32_t xy = d[0] | ((mask & 1u) << 15) | (d[1] << 16) | (((mask >> 1) & 1u) << 31);
+    if (m.rec == REC_WIDE) {
+        m.nbr[id] = make_uint2(xy, d[2]);
+        m.nbrp[id] = d[3];
+    } else {
+        m.nbr[id] = make_uint2(xy, d[2] | (d[3] << 16));
+    }
+}
+
 // ---- mbarrier and bulk (TMA) copies into shared memory
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {

@@ -224,7 +224,6 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
     const int last = slot_of(1, n - 1);
     const int32_t pbase = sBase[slot_of(1, 0)];
     const int32_t pend = sBase[last] + sPre[last * W + (W - 1)] + __popc(sP[last * WS + (W - 1)]);
-    int32_t reach = 1;
     for (int32_t id = pbase + tid; id < pend; id += nthr) {
         int lr = 0;
         for (int hi = n; hi - lr > 1;) { // the last own row whose first id is <= id
@@ -275,15 +274,10 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
             if ((mask >> f) & 1u) {
                 const int32_t nb = rank(nbs[f - 2], p);
                 *dst++ = nb;
-                const int32_t d = nb > id ? nb - id : id - nb;
-                reach = d > reach ? d : reach;
-                dist[f - 2] = (uint32_t)d & 0x7fffu;
+                dist[f - 2] = (uint32_t)(nb > id ? nb - id : id - nb);
             }
-        m.nbr[id] = make_uint2(dist[0] | ((mask & 1u) << 15) | (dist[1] << 16) | (((mask >> 1) & 1u) << 31),
-                               dist[2] | (dist[3] << 16));
+        store_record(m, id, mask, dist);
     }
-    reach = (int32_t)__reduce_max_sync(kFull, (unsigned)reach);
-    if (lane == 0 && reach > 1) atomicMax(m.meta, reach);
 
     // ---- quads of sample rows (cy, cz), cy = c0 - 1 + lr, in quad order: within
     // a word by bit, and at one bit x before y before z.  Thread k takes quad

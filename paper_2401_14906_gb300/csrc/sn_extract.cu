@@ -137,12 +137,13 @@ __global__ void __launch_bounds__(256, 4) k_count(const T *__restrict__ lab, Cla
 }
 
 // Single-map scan: tiles are numbered by a ticket in the order blocks start.
-__global__ void __launch_bounds__(kScanThreads) k_scan(Geometry g, ExtractScratch s, DevTotals *tot, int ntiles)
+__global__ void __launch_bounds__(kScanThreads) k_scan(Geometry g, ExtractScratch s, DevTotals *tot, int ntiles,
+                                                       int spin_limit)
 {
     __shared__ int tile_sh;
     if (threadIdx.x == 0) tile_sh = (int)atomicAdd(s.scan_ticket, 1u);
     __syncthreads();
-    scan_tile(g, s, tot, tile_sh, ntiles);
+    scan_tile(g, s, tot, tile_sh, ntiles, spin_limit);
 }
 
 
@@ -199,7 +200,6 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 3) k_emit(const T *__restrict
     const T *srow = lab + (has_srow ? rs : 0) * g.nx;
     int run[6] = {0, 0, 0, 0, 0, 0};
     int srun = 0, qrun = 0;
-    int32_t reach = 1; // largest |neighbour id - id| seen by this lane (the -x/+x neighbours are 1 away)
     uint32_t carry[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
     for (int64_t w0 = 0; w0 < W; w0 += kSeg) {
@@ -310,12 +310,9 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 3) k_emit(const T *__restrict
                     const int32_t nb =
                         (int32_t)(base[f - 1] + sh.pre[wp][f - 1][wl] + __popc(sh.P[wp][f - 1][wl] & lt));
                     *dst++ = nb;
-                    const int32_t d = nb > id ? nb - id : id - nb;
-                    reach = d > reach ? d : reach;
-                    dist[f - 2] = (uint32_t)d & 0x7fffu;
+                    dist[f - 2] = (uint32_t)(nb > id ? nb - id : id - nb);
                 }
-            m.nbr[id] = make_uint2(dist[0] | ((mask & 1u) << 15) | (dist[1] << 16) | (((mask >> 1) & 1u) << 31),
-                                   dist[2] | (dist[3] << 16));
+            store_record(m, id, mask, dist);
         }
         __syncwarp();
 
@@ -376,8 +373,6 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 3) k_emit(const T *__restrict
             __syncwarp();
         }
     }
-    reach = (int32_t)__reduce_max_sync(kFull, (unsigned)reach);
-    if (lane == 0) atomicMax(m.meta, reach);
 }
 
 template <typename T, int MODE>
@@ -630,11 +625,17 @@ cudaError_t launch_scan(const Geometry &g, const ExtractScratch &s, DevTotals *t
     cudaError_t e = cudaSuccess;
     if (clear) {
         if ((e = cudaMemsetAsync(s.scan_flags, 0, sizeof(int32_t) * (size_t)ntiles, st)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(s.scan_ticket, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(s.scan_ticket, 0, 2 * sizeof(uint32_t), st)) != cudaSuccess) return e;
     }
     ProfScope ps("k_scan", st);
-    k_scan<<<ntiles, kScanThreads, 0, st>>>(g, s, totals, ntiles);
+    k_scan<<<ntiles, kScanThreads, 0, st>>>(g, s, totals, ntiles, scan_spin_limit());
     return cudaGetLastError();
+}
+
+int rec_mode(const DevTotals &t)
+{
+    if (t.yreach >= kPackedReach) return REC_CSR;
+    return t.zreach < kPackedReach ? REC_COMPACT : REC_WIDE;
 }
 
 cudaError_t launch_emit(int type, const void *labels, const Classifier &c, const Geometry &g,

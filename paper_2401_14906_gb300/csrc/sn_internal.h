@@ -54,7 +54,7 @@ struct ExtractScratch {
     int64_t *offP, *offS, *offQ; // [Rc+1] exclusive prefix sums; [Rc] = totals
     int32_t *scan_flags;  // [tiles] look-back status
     int64_t *scan_vals;   // [2][3][tiles] aggregate / inclusive values
-    uint32_t *scan_ticket;// 1 counter
+    uint32_t *scan_ticket;// 2 counters: [0] numbers the scan tiles as they start, [1] counts the tiles done
 };
 
 // Totals read back by the host after the scan.
@@ -62,6 +62,18 @@ struct DevTotals {
     int64_t n_points, n_stencil, n_quads;
     int32_t error; // bit 0: look-back spin limit hit, bit 1: a label copy wait gave up
     int32_t pad;
+    // Upper bounds on the id distance between a point and its -y/+y (yreach) and
+    // -z/+z (zreach) neighbours: the most points in two consecutive cell rows and
+    // in two consecutive cell slices.  They fix the width of the sweep records.
+    int64_t yreach, zreach;
+};
+
+// How the smoothing sweeps find a point's neighbours (chosen per mesh from the
+// totals' reach bounds, before the emission writes the records).
+enum RecMode {
+    REC_COMPACT = 0, // nbr: 15-bit -y/+y and -z/+z distances (8 bytes per point)
+    REC_WIDE = 1,    // nbr: 15-bit -y/+y distances and the 32-bit -z distance, nbrp: the +z distance (12 bytes)
+    REC_CSR = 2,     // the CSR stencil (-y/+y distances beyond 15 bits: rows wider than 16382 samples)
 };
 
 // Output arrays of a mesh.
@@ -74,12 +86,15 @@ struct MeshArrays {
     int64_t *sten_off;   // [np+1]
     int32_t *sten_ids;   // [ns]
     uint8_t *face_mask;  // [np]
-    int32_t *meta;       // [4]: 0 = max |neighbour id - id| over all stencils, 1 = smoothing error flag
+    int32_t *meta;       // [4]: 1 = smoothing error flag (0, 2 and 3 are unused)
     float2 *lut_x, *lut_y, *lut_z; // [n+1] cell-centre world coordinate per axis for c = -1..n-1, as
                                    // (hi, lo): hi = the coordinate rounded to float, lo = the rest
-    uint2 *nbr;          // [np] packed neighbour record for the smoothing sweeps (valid while meta[0] < 2^15):
-                         //   .x = d(-y) | d(+y) << 16, .y = d(-z) | d(+z) << 16, each 15-bit |id distance|,
-                         //   0 = no neighbour; bit 15 of the -y / +y fields = -x / +x neighbour present
+    uint2 *nbr;          // [np] neighbour record for the smoothing sweeps (REC_COMPACT / REC_WIDE):
+                         //   .x = d(-y) | d(+y) << 16, each a 15-bit |id distance|, 0 = no neighbour, and
+                         //        bit 15 / 31 = -x / +x neighbour present;
+                         //   .y = d(-z) | d(+z) << 16 (15 bits each; REC_COMPACT) or d(-z) (REC_WIDE)
+    uint32_t *nbrp;      // [np] d(+z) (REC_WIDE only)
+    int rec;             // RecMode of this mesh
 };
 
 constexpr int32_t kPackedReach = 1 << 15; // packed records hold id distances below this
@@ -122,6 +137,10 @@ constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kSpinLimit = 1 << 22;
 
+// Bounded-wait limit of the scan's look-back (sn_api.cu): kSpinLimit unless a
+// test lowered it with sn_debug_set_spin_limit; < 0 makes every look-back give up.
+int scan_spin_limit();
+
 // launchers (sn_extract.cu)
 cudaError_t launch_planes(int type, const void *labels, const Classifier &c, const Geometry &g,
                           const ExtractScratch &s, cudaStream_t st);
@@ -141,6 +160,8 @@ cudaError_t launch_count_range(int type, const void *labels, const Classifier &c
 // clear = false: the scan flags and ticket are already zero
 cudaError_t launch_scan(const Geometry &g, const ExtractScratch &s, DevTotals *totals, cudaStream_t st,
                         bool clear = true);
+// record mode for a mesh whose totals are `t`
+int rec_mode(const DevTotals &t);
 cudaError_t launch_emit(int type, const void *labels, const Classifier &c, const Geometry &g,
                         const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st);
 

@@ -26,8 +26,32 @@ __device__ __forceinline__ void st_release(int *p, int v)
 // are bounded; on timeout the error bit is set and the tile finishes.  The
 // counts are read through L2 (they may have been written by other CTAs of the
 // same launch).  The last tile also stores the totals.
+//
+// The scan also bounds the id distance between a point and its face
+// neighbours, which fixes how wide the smoothing sweeps' neighbour records must
+// be: a -y/+y neighbour is at most the points of two consecutive cell rows
+// away, a -z/+z neighbour at most those of two consecutive cell slices.  Each
+// tile takes the largest sum of two adjacent row counts (one atomic max), and
+// the last tile to finish, which sees every row offset, the largest sum over
+// two adjacent slices.  spin_limit < 0: every look-back gives up at once.
+__device__ __forceinline__ int64_t block_max64(int64_t v, int64_t *red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int64_t t = __shfl_xor_sync(kFull, v, o);
+        v = t > v ? t : v;
+    }
+    __syncthreads(); // red may still be read by a previous call
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    int64_t m = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
+    return m;
+}
+
 __device__ __forceinline__ void scan_tile(const Geometry &g, const ExtractScratch &s, DevTotals *tot, int tile,
-                                          int ntiles)
+                                          int ntiles, int spin_limit)
 {
     __shared__ int64_t warp_tot[kScanThreads / 32][3];
     __shared__ int64_t tile_excl[3];
@@ -80,10 +104,10 @@ __device__ __forceinline__ void scan_tile(const Geometry &g, const ExtractScratc
             while (!done) {
                 const int idx = pred - lane;
                 int f = 0;
-                if (idx >= 0) {
+                if (idx >= 0 && spin_limit >= 0) {
                     int spins = 0;
                     f = ld_acquire(&s.scan_flags[idx]);
-                    while (f == 0 && spins < kSpinLimit) {
+                    while (f == 0 && spins < spin_limit) {
                         __nanosleep(64);
                         f = ld_acquire(&s.scan_flags[idx]);
                         ++spins;
@@ -132,6 +156,37 @@ __device__ __forceinline__ void scan_tile(const Geometry &g, const ExtractScratc
         tot->n_stencil = ts;
         tot->n_quads = tq;
     }
+
+    // ---- reach bounds: adjacent cell rows here, adjacent cell slices in the last tile to finish
+    __shared__ int64_t red[kScanThreads / 32];
+    __shared__ int last_sh;
+    int64_t ymax = 0;
+    {
+        const int64_t nxt = base + kScanItems < g.Rc ? (int64_t)__ldcg(s.cntP + base + kScanItems) : 0;
+#pragma unroll
+        for (int t = 0; t < kScanItems; ++t) {
+            const int64_t pair = v[0][t] + (t + 1 < kScanItems ? v[0][t + 1] : nxt);
+            ymax = pair > ymax ? pair : ymax;
+        }
+    }
+    ymax = block_max64(ymax, red);
+    if (tid == 0) {
+        if (ymax > 0) atomicMax(reinterpret_cast<unsigned long long *>(&tot->yreach), (unsigned long long)ymax);
+        __threadfence(); // this tile's offsets (and the totals) before its ticket
+        last_sh = atomicAdd(s.scan_ticket + 1, 1u) == (unsigned)(ntiles - 1);
+    }
+    __syncthreads();
+    if (!last_sh) return;
+    __threadfence();
+    const int64_t ny1 = g.ny + 1, nz1 = g.nz + 1;
+    int64_t zmax = 0;
+    for (int64_t c = tid; c + 1 < nz1; c += kScanThreads) {
+        const int64_t hi = (c + 2) * ny1 < g.Rc ? (c + 2) * ny1 : g.Rc;
+        const int64_t pair = __ldcg(s.offP + hi) - __ldcg(s.offP + c * ny1);
+        zmax = pair > zmax ? pair : zmax;
+    }
+    zmax = block_max64(zmax, red);
+    if (tid == 0) tot->zreach = zmax;
 }
 
 } // namespace dev

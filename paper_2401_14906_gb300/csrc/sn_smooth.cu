@@ -11,7 +11,7 @@ using namespace dev;
 // One Jacobi sweep over kSweepPoints points per CTA.
 __global__ void __launch_bounds__(kSweepThreads) k_smooth(SweepArgs a)
 {
-    sweep_block<false>(a, blockIdx.x * (uint32_t)kSweepPoints, a.meta[0] >= kPackedReach);
+    sweep_block<false>(a, blockIdx.x * (uint32_t)kSweepPoints);
 }
 
 __global__ void __launch_bounds__(256) k_centres(MeshArrays m, int64_t np)
@@ -46,6 +46,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_smooth_batch(const SmoothBatc
     a.oin = mp.buf[t & 1];
     a.oout = mp.buf[(t & 1) ^ 1];
     a.nbr = mp.m.nbr;
+    a.nbrp = mp.m.nbrp;
+    a.rec = mp.m.rec;
     a.soff = mp.m.sten_off;
     a.sids = mp.m.sten_ids;
     a.fmask = mp.m.face_mask;
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_smooth_batch(const SmoothBatc
     a.first = t == 0;
     a.last = t == iterations - 1;
     a.sphere = sphere;
-    sweep_block<false>(a, (b - block_start[lo]) * (uint32_t)kSweepPoints, a.meta[0] >= kPackedReach);
+    sweep_block<false>(a, (b - block_start[lo]) * (uint32_t)kSweepPoints);
 }
 
 // world positions from the offsets in `o`
@@ -120,6 +122,8 @@ cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float
     if (iterations == 0) return launch_centres(m, np, st);
     SweepArgs a;
     a.nbr = m.nbr;
+    a.nbrp = m.nbrp;
+    a.rec = m.rec;
     a.soff = m.sten_off;
     a.sids = m.sten_ids;
     a.fmask = m.face_mask;
@@ -175,6 +179,8 @@ cudaError_t launch_smooth_from(const MeshArrays &m, int64_t np, int iterations, 
     }
     SweepArgs a;
     a.nbr = m.nbr;
+    a.nbrp = m.nbrp;
+    a.rec = m.rec;
     a.soff = m.sten_off;
     a.sids = m.sten_ids;
     a.fmask = m.face_mask;

@@ -9,12 +9,16 @@
 // reads buffer t and writes buffer t+1 (the double buffer of Sec. 2.4); the last
 // sweep also writes the world coordinates.
 //
-// A point's neighbours come from an 8-byte record written during extraction:
-// the -x/+x neighbours are always id-1/id+1 (one presence bit each), and the
-// -y/+y/-z/+z neighbours are stored as 15-bit id distances (0 = absent).  Per
-// point a sweep streams 12 B in + 12 B out + 8 B of neighbour record from HBM;
-// neighbours are gathered from L2 or L1.  Meshes whose neighbour distances do
-// not fit 15 bits use the CSR stencil instead.
+// A point's neighbours come from a record written during extraction: the
+// -x/+x neighbours are always id-1/id+1 (one presence bit each), and the
+// -y/+y/-z/+z neighbours are stored as id distances (0 = absent).  While every
+// distance fits 15 bits the record is 8 bytes (REC_COMPACT); meshes whose
+// slices hold too many points for that (the 1024^2 x 512 connectome-like map)
+// keep the -z/+z distances in 32 bits, 12 bytes per point (REC_WIDE: the -z
+// distance in the second word of the 8-byte record, the +z one in a separate
+// array).  Per point a sweep streams 12 B in + 12 B out + the record from HBM;
+// neighbours are gathered from L2 or L1.  Rows of more than 16382 samples,
+// whose -y/+y distances may not fit 15 bits, use the CSR stencil (REC_CSR).
 #pragma once
 
 #include "sn_internal.h"
@@ -31,6 +35,7 @@ struct SweepArgs {
     const float *oin;
     float *oout;
     const uint2 *nbr;
+    const uint32_t *nbrp;
     const int64_t *soff;
     const int32_t *sids;
     const uint8_t *fmask;
@@ -43,6 +48,12 @@ struct SweepArgs {
     float spx, spy, spz;
     int first, last; // first sweep: offsets are all zero; last sweep: also write world coordinates
     int sphere;      // constrain |o| <= h instead of |o_a| <= h per axis
+    int rec;         // RecMode of the mesh
+};
+
+// A point's decoded record: -x/+x presence and the four id distances.
+struct Nbr {
+    uint32_t xy, dmz, dpz;
 };
 
 // The constraint of Sec. 2.2: a box of half-width h per axis, or a ball of radius h.
@@ -73,12 +84,12 @@ template <bool COH> __device__ __forceinline__ float3 ld3(const float *__restric
     return make_float3(q[0], q[1], q[2]);
 }
 
-// Neighbour sum and update of one point (packed neighbour record).
-template <bool COH> __device__ __forceinline__ void sweep_point(const SweepArgs &a, uint32_t i, float3 o, uint2 r)
+// Neighbour sum and update of one point (neighbour record).
+template <bool COH> __device__ __forceinline__ void sweep_point(const SweepArgs &a, uint32_t i, float3 o, Nbr r)
 {
     const float *__restrict__ oin = a.oin;
-    const uint32_t mx = (r.x >> 15) & 1u, px = r.x >> 31;
-    const uint32_t dmy = r.x & 0x7fffu, dpy = (r.x >> 16) & 0x7fffu, dmz = r.y & 0xffffu, dpz = r.y >> 16;
+    const uint32_t mx = (r.xy >> 15) & 1u, px = r.xy >> 31;
+    const uint32_t dmy = r.xy & 0x7fffu, dpy = (r.xy >> 16) & 0x7fffu, dmz = r.dmz, dpz = r.dpz;
     const int n = (int)(mx + px + (dmy != 0) + (dpy != 0) + (dmz != 0) + (dpz != 0));
     float3 acc = make_float3((float)((int)px - (int)mx), (float)((int)(dpy != 0) - (int)(dmy != 0)),
                              (float)((int)(dpz != 0) - (int)(dmz != 0)));
@@ -153,8 +164,7 @@ constexpr int kSweepThreads = 256, kSweepPoints = 2 * kSweepThreads; // two poin
 // updates PPT points kSweepThreads apart; the own offsets and neighbour records
 // of all of them are loaded before any point's neighbours are gathered, so that
 // PPT times as many loads are in flight.  The first sweep starts from zero
-// offsets and reads none.  `csr`: the neighbour distances do not fit the packed
-// record.
+// offsets and reads none.  The record mode a.rec is the same in every thread.
 //
 // Sweeps after the first are launched as programmatic dependents of the sweep
 // before them: every block lets the next sweep's blocks be scheduled at once,
@@ -163,11 +173,11 @@ constexpr int kSweepThreads = 256, kSweepPoints = 2 * kSweepThreads; // two poin
 // writes any offsets.  A launch without that attribute returns from the wait
 // at once.
 template <bool COH, int PPT = 2>
-__device__ __forceinline__ void sweep_block(const SweepArgs &a, uint32_t base, bool csr)
+__device__ __forceinline__ void sweep_block(const SweepArgs &a, uint32_t base)
 {
     const uint64_t np = (uint64_t)a.np;
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    if (csr) {
+    if (a.rec == REC_CSR) {
         asm volatile("griddepcontrol.wait;" ::: "memory");
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
@@ -177,11 +187,20 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, uint32_t base, b
         return;
     }
     float3 o[PPT];
-    uint2 r[PPT];
+    Nbr r[PPT];
+    const bool wide = a.rec == REC_WIDE;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         const uint32_t i = base + threadIdx.x + q * kSweepThreads;
-        r[q] = i < np ? a.nbr[i] : make_uint2(0u, 0u);
+        const uint2 v = i < np ? a.nbr[i] : make_uint2(0u, 0u);
+        r[q].xy = v.x;
+        if (wide) {
+            r[q].dmz = v.y;
+            r[q].dpz = i < np ? a.nbrp[i] : 0u;
+        } else {
+            r[q].dmz = v.y & 0xffffu;
+            r[q].dpz = v.y >> 16;
+        }
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
 #pragma unroll

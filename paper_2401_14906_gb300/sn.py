@@ -53,6 +53,7 @@ SIGNATURES = {
     "sn_mesh_device_arrays": (ctypes.c_int, [_P] + [ctypes.POINTER(_P)] * 6),
     "sn_mesh_face_masks": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
     "sn_mesh_cells": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "sn_mesh_record_bytes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "sn_mesh_copy_to_host": (ctypes.c_int, [_P] + [_P] * 6),
     "sn_mesh_copy_to_host_async": (ctypes.c_int, [_P] + [_P] * 6),
     "sn_mesh_wait": (ctypes.c_int, [_P]),
@@ -80,6 +81,10 @@ SIGNATURES = {
     "sn_learner_step": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float]),
     "sn_profile_enable": (None, [ctypes.c_int]),
     "sn_profile_read": (ctypes.c_int, [ctypes.POINTER(sn_kernel_time), ctypes.c_int, ctypes.c_int]),
+    "sn_debug_set_spin_limit": (None, [ctypes.c_int]),
+    "sn_debug_fail_allocation": (None, [ctypes.c_int64]),
+    "sn_debug_set_point_limit": (None, [ctypes.c_int64]),
+    "sn_debug_reset": (None, []),
 }
 
 
@@ -548,3 +553,31 @@ def sn_learn_gradient(learner: Learner, x, t):
 
 def sn_learner_step(learner: Learner, grads, lr, weight_decay=0.0):
     _check(load().sn_learner_step(learner.handle, ctypes.c_void_p(grads.data_ptr()), float(lr), float(weight_decay)))
+
+
+# ------------------------------------------------------------ failure injection
+def sn_debug_set_spin_limit(n: int):
+    """Polls after which the row scan's look-back gives up (< 0: at once); see include/sn.h."""
+    load().sn_debug_set_spin_limit(int(n))
+
+
+def sn_debug_fail_allocation(k: int):
+    """Make the k-th library allocation from now fail (k < 0: off)."""
+    load().sn_debug_fail_allocation(int(k))
+
+
+def sn_debug_set_point_limit(n: int):
+    """Extractions of more than n points return SN_EOVERFLOW (n < 0: INT32_MAX)."""
+    load().sn_debug_set_point_limit(int(n))
+
+
+def sn_debug_reset():
+    """Restore the default spin limit, allocation behaviour and point limit."""
+    load().sn_debug_reset()
+
+
+def sn_mesh_record_bytes(mesh) -> int:
+    """Bytes per point of the sweeps' neighbour record: 8, 12, or 0 (the CSR stencil)."""
+    b = ctypes.c_int()
+    _check(load().sn_mesh_record_bytes(mesh.handle, ctypes.byref(b)))
+    return b.value

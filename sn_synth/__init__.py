@@ -17,6 +17,8 @@ available here):
 * ``config3``  1024x1024x512 uint32 connectomics-like map (connectome stand-in):
   50,000 Voronoi cells with sample spacing (1,1,4) and 5% background gaps along
   cell faces, seed 3.
+* ``config3_slab``  1024x1024x64 uint32 with the connectome's cell density (for
+  profiler captures of the same kernels at a few GB of device memory).
 * ``config5_maps``  256 maps of uneven sizes (edges 32-256), uint8/uint16, 1-20
   ellipsoid or Voronoi labels, seeds 5000-5255.
 * ``config4_train_map``  256^3 uint16 training maps (alternating Voronoi with
@@ -174,6 +176,14 @@ def config2(dims=(512, 512, 512)):
 def config3(dims=(1024, 1024, 512), n_seeds=50000):
     """1024x1024x512 uint32 connectomics-like map, 50k cells, spacing (1,1,4), 8 iterations."""
     return Workload("c3_1024x1024x512_u32_connectome", connectome(dims, n_seeds, 4, seed=3),
+                    spacing=(1.0, 1.0, 4.0), iterations=8)
+
+
+def config3_slab(nz=64):
+    """A slab of the connectomics-like map's shape: 1024x1024xnz uint32 with the same cell density
+    (50,000 * nz / 512 cells), spacing (1,1,4), 8 iterations -- small enough for a profiler capture."""
+    return Workload("c3slab_1024x1024x%d_u32_connectome" % nz,
+                    connectome((1024, 1024, nz), max(1, 50000 * nz // 512), 4, seed=3),
                     spacing=(1.0, 1.0, 4.0), iterations=8)
 
 

@@ -132,14 +132,36 @@ def test_degenerate_and_empty():
     parity(((x + y + z) % 2).astype(np.uint8), iterations=5)
 
 
-def test_wide_slices_use_the_stencil_fallback():
+def _record_bytes(lab):
+    from paper_2401_14906_gb300 import sn
+    m = sn.sn_extract(lab)
+    b = sn.sn_mesh_record_bytes(m)
+    m.free()
+    return b
+
+
+def test_wide_slices_use_the_wide_record():
     # a checkerboard with 261x261 cells per slice: -z/+z neighbours are ~68k ids
-    # apart, beyond the 15-bit packed neighbour record, so the sweeps read the CSR
+    # apart, beyond the 15-bit fields of the 8-byte record, so the sweeps read
+    # 32-bit -z/+z distances (12-byte record)
     z, y, x = np.mgrid[0:3, 0:260, 0:260]
-    parity(((x + y + z) % 2).astype(np.uint8), iterations=6)
-    # and a map just below the limit in the same run of tests
-    z, y, x = np.mgrid[0:3, 0:150, 0:150]
-    parity(((x + y + z) % 2).astype(np.uint8), iterations=6)
+    lab = ((x + y + z) % 2).astype(np.uint8)
+    assert _record_bytes(lab) == 12
+    parity(lab, iterations=6)
+    # and a map below the limit in the same run of tests
+    z, y, x = np.mgrid[0:3, 0:120, 0:120]
+    lab = ((x + y + z) % 2).astype(np.uint8)
+    assert _record_bytes(lab) == 8
+    parity(lab, iterations=6)
+
+
+def test_very_wide_dense_rows_use_the_stencil():
+    # 20,000 samples per row alternating between two labels: every cell row holds
+    # ~20k points, so -y/+y distances may exceed 15 bits and the sweeps read the CSR
+    z, y, x = np.mgrid[0:3, 0:3, 0:20000]
+    lab = ((x + y + z) % 2).astype(np.uint16)
+    assert _record_bytes(lab) == 0
+    parity(lab, iterations=5)
 
 
 def test_very_wide_rows_use_the_per_row_kernels():
@@ -209,9 +231,10 @@ def test_config2_full_size():
 
 def test_config3_full_size():
     # 1024x1024x512 uint32, 50,000 Voronoi cells with (1,1,4) spacing and 5% gaps:
-    # ~1.4e8 points, whose -z/+z neighbours are beyond the packed record's reach,
-    # so the sweeps take the CSR path at full size
+    # ~1.4e8 points, whose -z/+z neighbours are beyond the 15-bit fields, so the
+    # sweeps read the 12-byte record at full size
     w = sn_synth.config3()
+    assert _record_bytes(w.labels[:64]) == 12
     ref = parity(w.labels, w.spacing, w.origin, iterations=w.iterations, relaxation=w.relaxation,
                  constraint=w.constraint)
     assert ref.n_points > 100_000_000
