@@ -34,6 +34,9 @@ struct sn_mesh {
     cudaEvent_t copied;    // the last sn_mesh_copy_to_host_async has finished
     int32_t *copy_meta;    // its copy of the meta words (pinned)
     bool copy_pending;
+    // The extraction does not write the offsets (a smoothing overwrites them all);
+    // until something does, they are zeroed when first handed out (ensure_offsets).
+    bool offsets_pending;
 };
 
 // A label map copied to the device ahead of its extraction (sn_labels_upload).
@@ -167,6 +170,17 @@ struct ProfEntry {
 std::map<std::string, ProfEntry> g_prof;
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// Zeroes a mesh's offsets on its stream if nothing has written them yet (an
+// extraction that no smoothing followed): the state in which they are handed out.
+cudaError_t ensure_offsets(const sn_mesh *cm)
+{
+    sn_mesh *m = const_cast<sn_mesh *>(cm);
+    if (!m->offsets_pending || m->np == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(m->a.offsets, 0, sizeof(float) * 3 * (size_t)m->np, m->stream);
+    if (e == cudaSuccess) m->offsets_pending = false;
+    return e;
+}
 
 } // namespace
 
@@ -543,7 +557,7 @@ sn_status job_allocate(ExtractJob &j, cudaStream_t st, bool with_smooth_buffer =
     m->np = np;
     m->nq = nq;
     m->ns = ns;
-    m->a.rec = sn::rec_mode(*htot);
+    m->a.rec = sn::rec_mode(*htot, &m->a.by, &m->a.bz);
     const int64_t nx = j.dims[0], ny = j.dims[1], nz = j.dims[2];
     struct {
         void **p;
@@ -580,6 +594,7 @@ sn_status job_allocate(ExtractJob &j, cudaStream_t st, bool with_smooth_buffer =
     }
     if (smooth_bytes) m->smooth_scratch = reinterpret_cast<float *>(block);
     if (m->a.rec != sn::REC_WIDE) m->a.nbrp = nullptr; // (given no bytes above)
+    m->offsets_pending = true;
     m->a.lut_y = m->a.lut_x + (nx + 1);
     m->a.lut_z = m->a.lut_y + (ny + 1);
     j.mesh = m;
@@ -838,6 +853,7 @@ sn_status sn_smooth_ex(sn_mesh *m, int iterations, float relaxation, float const
     cudaError_t e = sn::launch_smooth(m->a, m->np, iterations, relaxation, 0.5f * constraint_distance,
                                       constraint == SN_CONSTRAINT_SPHERE, m->smooth_scratch, m->spacing, m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "smoothing launch");
+    m->offsets_pending = false; // every offset is written
     return SN_OK;
 }
 
@@ -877,6 +893,10 @@ sn_status sn_mesh_device_arrays(const sn_mesh *m, const float **points, const in
                                 const int32_t **stencil_ids, const float **offsets)
 {
     if (!m) return fail(SN_EINVAL, "mesh is NULL");
+    if (offsets) {
+        cudaError_t e = ensure_offsets(m);
+        if (e != cudaSuccess) return cuda_fail(e, "offsets");
+    }
     if (points) *points = m->a.points;
     if (quads) *quads = m->a.quads;
     if (quad_labels) *quad_labels = m->a.quad_labels;
@@ -903,7 +923,7 @@ sn_status sn_mesh_cells(const sn_mesh *m, const uint64_t **cells)
 sn_status sn_mesh_record_bytes(const sn_mesh *m, int *bytes_per_point)
 {
     if (!m || !bytes_per_point) return fail(SN_EINVAL, "mesh or output is NULL");
-    *bytes_per_point = m->a.rec == sn::REC_COMPACT ? 8 : m->a.rec == sn::REC_WIDE ? 12 : 0;
+    *bytes_per_point = m->a.rec == sn::REC_PACKED ? 8 : m->a.rec == sn::REC_WIDE ? 12 : 0;
     return SN_OK;
 }
 
@@ -911,6 +931,10 @@ sn_status sn_mesh_copy_to_host(const sn_mesh *m, float *points, int32_t *quads, 
                                int64_t *stencil_offsets, int32_t *stencil_ids, float *offsets)
 {
     if (!m) return fail(SN_EINVAL, "mesh is NULL");
+    if (offsets) {
+        cudaError_t e0 = ensure_offsets(m);
+        if (e0 != cudaSuccess) return cuda_fail(e0, "offsets");
+    }
     struct {
         void *dst;
         const void *src;
@@ -991,7 +1015,8 @@ sn_status sn_mesh_copy_to_host_async(sn_mesh *m, float *points, int32_t *quads, 
     cudaStream_t cs = d2h_stream(m->device);
     int32_t *meta = meta_slot();
     if (!cs || !meta) return fail(SN_ENOMEM, "copy stream or pinned meta slot");
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = offsets ? ensure_offsets(m) : cudaSuccess; // (on the mesh's stream, before `smoothed`)
+    if (e != cudaSuccess) return cuda_fail(e, "offsets");
     if (!m->copied && (e = cudaEventCreateWithFlags(&m->copied, cudaEventDisableTiming)) != cudaSuccess) {
         m->copied = nullptr;
         return cuda_fail(e, "copy event");
@@ -1187,7 +1212,8 @@ sn_status sn_learner_add_examples(sn_learner *l, const sn_mesh *m, float constra
         return fail(SN_EINVAL, "constraint distance must be finite and >= 0");
     if (m->np == 0) return SN_OK;
     // the mesh's work must be complete before the learner's stream reads it
-    cudaError_t e = cudaStreamSynchronize(m->stream);
+    cudaError_t e = ensure_offsets(m);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "mesh stream");
     const int64_t need = l->n + m->np;
     if (need > l->cap) {
@@ -1357,6 +1383,7 @@ sn_status sn_smooth_learned(sn_mesh *m, const sn_learner *l, int corrections, fl
         e = sn::launch_smooth_from(m->a, m->np, corrections, relaxation, half, sphere, start,
                                    start == m->a.offsets ? m->smooth_scratch : m->a.offsets, m->spacing, m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "learned smoothing launch");
+    m->offsets_pending = false; // every offset is written
     return SN_OK;
 }
 
@@ -1721,6 +1748,7 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
     }
     for (int64_t i = 0; i < n_maps; ++i) {
         jobs[i].mesh->stream = st;
+        jobs[i].mesh->offsets_pending = iterations == 0; // else the sweeps wrote every offset
         out[i] = jobs[i].mesh;
     }
     return finish(SN_OK);

@@ -81,18 +81,48 @@ __device__ __forceinline__ int64_t sample_row(const Geometry &g, int64_t y, int6
 __device__ __forceinline__ uint32_t shl1(uint32_t cur, uint32_t prev) { return (cur << 1) | (prev >> 31); }
 
 // The sweeps' neighbour record of point id (face mask, |id distance| to the
-// -y/+y/-z/+z neighbours, 0 = absent) in the mesh's record mode; the reach
-// bounds that chose the mode guarantee that the distances fit its fields.
+// -y/+y/-z/+z neighbours, 0 = absent) in the mesh's record mode (RecMode); the
+// reach bounds that chose the mode guarantee that the distances fit its fields.
 __device__ __forceinline__ void store_record(const MeshArrays &m, int32_t id, uint32_t mask, const uint32_t (&d)[4])
 {
     if (m.rec == REC_CSR) return;
-    const uint32_t xy = d[0] | ((mask & 1u) << 15) | (d[1] << 16) | (((mask >> 1) & 1u) << 31);
+    const uint32_t flags = (mask & 1u) | (((mask >> 1) & 1u) << 1);
     if (m.rec == REC_WIDE) {
-        m.nbr[id] = make_uint2(xy, d[2]);
+        m.nbr[id] = make_uint2(flags | (d[0] << 2) | (d[1] << 17), d[2]);
         m.nbrp[id] = d[3];
-    } else {
-        m.nbr[id] = make_uint2(xy, d[2] | (d[3] << 16));
+        return;
     }
+    const int by = m.by, bz = m.bz;
+    const uint64_t r = (uint64_t)flags | ((uint64_t)d[0] << 2) | ((uint64_t)d[1] << (2 + by)) |
+                       ((uint64_t)d[2] << (2 + 2 * by)) | ((uint64_t)d[3] << (2 + 2 * by + bz));
+    m.nbr[id] = make_uint2((uint32_t)r, (uint32_t)(r >> 32));
+}
+
+// A decoded neighbour record: -x/+x presence (0/1) and the four id distances.
+struct NbrDist {
+    uint32_t mx, px, dmy, dpy, dmz, dpz;
+};
+
+// Decodes record v (and, for REC_WIDE, the +z distance p) of a mesh in mode rec.
+__device__ __forceinline__ NbrDist decode_record(uint2 v, uint32_t p, int rec, int by, int bz)
+{
+    NbrDist d;
+    d.mx = v.x & 1u;
+    d.px = (v.x >> 1) & 1u;
+    if (rec == REC_WIDE) {
+        d.dmy = (v.x >> 2) & 0x7fffu;
+        d.dpy = v.x >> 17;
+        d.dmz = v.y;
+        d.dpz = p;
+        return d;
+    }
+    const uint64_t r = ((uint64_t)v.y << 32) | v.x;
+    const uint64_t my = (1ull << by) - 1ull, mz = (1ull << bz) - 1ull;
+    d.dmy = (uint32_t)((r >> 2) & my);
+    d.dpy = (uint32_t)((r >> (2 + by)) & my);
+    d.dmz = (uint32_t)((r >> (2 + 2 * by)) & mz);
+    d.dpz = (uint32_t)(r >> (2 + 2 * by + bz));
+    return d;
 }
 
 // ---- mbarrier and bulk (TMA) copies into shared memory

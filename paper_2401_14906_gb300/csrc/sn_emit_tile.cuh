@@ -10,44 +10,43 @@ namespace dev {
 
 constexpr int kTileRows = 24;  // cell rows per tile of the single-map kernel
 constexpr int kTileMaxW = 64;  // rows of up to 2047 cells; wider rows use the per-row kernel
+constexpr int kListCap = 2048; // entries of the tile's position list (one chunk of points or quads)
 
 // shared-memory carve-up, in 4-byte words; every array starts on 16 bytes
 struct TileSmem {
-    int bar, P, planes, pre, base, F, dpre, qpre, soff, qoff, total;
+    int bar, P, planes, pre, base, F, dpre, qpre, soff, qoff, list, total;
     __host__ __device__ static int up4(int v) { return (v + 3) & ~3; }
     __host__ __device__ TileSmem(int ty, int W, int WS)
     {
         const int ns = 3 * (ty + 2);
         bar = 0;                               // one mbarrier, padded to 16 bytes
         P = 4;                                 // [ns][WS] point-plane words
-        planes = P + ns * WS;                  // [2 dk][3 plane][ty+1 rows][WS] X/Y/Z words
-        pre = planes + 2 * 3 * (ty + 1) * WS;  // [ns][W] points before the word, within the row
-        base = pre + up4(ns * W);              // [ns] first point id of the row
+        planes = P + ns * WS;                  // [5 plane][ty+1 rows][WS]: X, Y, Z of slice cz, X, Y of cz+1
+        pre = planes + 5 * (ty + 1) * WS;      // [ns][W] uint16 points before the word, within the row
+        base = pre + up4((ns * W + 1) / 2);    // [ns] first point id of the row
         F = base + up4(ns);                    // [ty][6][W] face planes of own rows
-        dpre = F + up4(ty * 6 * W);            // [ty][W] stencil entries before the word
-        qpre = dpre + up4(ty * W);             // [ty][W] quads before the word
-        soff = qpre + up4(ty * W);             // [ty] int64 first stencil entry of the row
+        dpre = F + up4(ty * 6 * W);            // [ty][W] uint16 stencil entries before the word
+        qpre = dpre + up4((ty * W + 1) / 2);   // [ty][W] uint16 quads before the word
+        soff = qpre + up4((ty * W + 1) / 2);   // [ty] int64 first stencil entry of the row
         qoff = soff + 2 * ty;                  // [ty] int64 first quad of the sample row
-        total = qoff + 2 * ty;
+        list = qoff + 2 * ty;                  // [kListCap] positions of one chunk of points or quads
+        total = list + kListCap;
     }
 };
-
-// position of the set bit of `word` with `nth` set bits below it (nth counted
-// from 0); 31 when the word has no more than nth set bits
-__device__ __forceinline__ int nth_bit(uint32_t word, int nth)
-{
-    int b = 0;
-#pragma unroll
-    for (int st = 16; st > 0; st >>= 1)
-        if (__popc(word & ((1u << (b + st)) - 1u)) <= nth) b += st;
-    return b;
-}
 
 // One tile (bx = run of cell rows, by = cz + 1) of the emission.  Label rows
 // are g.lp elements apart.  Counts, offsets and totals are read through L2, and
 // the bit planes (written by ordinary stores of the counting pass) by bulk
 // copies after a proxy fence.  Returns false (in every thread) when the staging
 // wait gave up; the copies may then still be in flight.
+//
+// After staging, the tile's points (and then its quads) are written in id
+// order in chunks of kListCap: for each chunk, one thread per (row, word)
+// lists the positions of the word's points that fall in the chunk (a loop over
+// the word's set bits), and then one thread per id takes its position from the
+// list -- consecutive threads write consecutive ids.  Within-row prefixes
+// (points, stencil entries and quads before each word) are uint16: a row holds
+// at most 2048 cells.
 template <typename T, int MODE>
 __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Classifier &c, const Geometry &g,
                                           const ExtractScratch &s, const MeshArrays &m, DevTotals *tot,
@@ -55,7 +54,7 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
 {
     extern __shared__ __align__(128) uint32_t sm[];
     const int TY = tg.ty, W = tg.W, WS = tg.WS, NS = tg.ns;
-    const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
+    const int tid = threadIdx.x, nthr = blockDim.x;
     const int64_t ny = g.ny, nz = g.nz, ny1 = ny + 1, nz1 = nz + 1;
     const int64_t c0 = bx * TY; // first cy + 1 of the tile
     const int64_t czc = by;     // cz + 1
@@ -65,13 +64,14 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.bar);
     uint32_t *sP = sm + L.P;
     uint32_t *sPl = sm + L.planes;
-    int32_t *sPre = reinterpret_cast<int32_t *>(sm + L.pre);
+    uint16_t *sPre = reinterpret_cast<uint16_t *>(sm + L.pre);
     int32_t *sBase = reinterpret_cast<int32_t *>(sm + L.base);
     uint32_t *sF = sm + L.F;
-    int32_t *sDpre = reinterpret_cast<int32_t *>(sm + L.dpre);
-    int32_t *sQpre = reinterpret_cast<int32_t *>(sm + L.qpre);
+    uint16_t *sDpre = reinterpret_cast<uint16_t *>(sm + L.dpre);
+    uint16_t *sQpre = reinterpret_cast<uint16_t *>(sm + L.qpre);
     int64_t *sSoff = reinterpret_cast<int64_t *>(sm + L.soff);
     int64_t *sQoff = reinterpret_cast<int64_t *>(sm + L.qoff);
+    uint32_t *sList = sm + L.list;
     const int64_t NP = __ldcg(&tot->n_points), NQ = __ldcg(&tot->n_quads), NS_ = __ldcg(&tot->n_stencil);
 
     // own cell row lr in [0, n): cy = c0 - 1 + lr; its sample row (cy, cz) exists iff cy >= 0 && cz >= 0
@@ -86,7 +86,8 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
 
     // ---- staging: runs of rows copied by TMA; rows outside the volume are zeroed.
     // point-plane slot (dz, lr) = dz * (TY + 2) + lr + 1, dz 0/1/2 = slices cz-1/cz/cz+1, lr in [-1, TY]
-    // plane row (dk, p, lr) = (dk * 3 + p) * (TY + 1) + lr: sample row j = c0 - 1 + lr of slice cz + dk
+    // plane row (q, lr) = q * (TY + 1) + lr, q = 3 dk + axis: sample row j = c0 - 1 + lr of slice cz + dk
+    // (slice cz + 1 needs only its X and Y rows)
     int pr_lo[3], pr_hi[3]; // point-plane rows [lo, hi) copied for each dz, in lr
     for (int dz = 0; dz < 3; ++dz) {
         const int64_t czz = czc - 1 + dz;
@@ -112,8 +113,8 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
         if (lr < pr_lo[dz] || lr >= pr_hi[dz])
             for (int w = 0; w < WS; ++w) sP[slot * WS + w] = 0u;
     }
-    for (int r = tid; r < 6 * (TY + 1); r += nthr) {
-        const int dk = r / (3 * (TY + 1)), lr = r % (TY + 1);
+    for (int r = tid; r < 5 * (TY + 1); r += nthr) {
+        const int q = r / (TY + 1), lr = r - q * (TY + 1), dk = q >= 3 ? 1 : 0;
         if (lr < pl_lo[dk] || lr >= pl_hi[dk])
             for (int w = 0; w < WS; ++w) sPl[r * WS + w] = 0u;
     }
@@ -123,7 +124,7 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
         asm volatile("fence.proxy.async.global;" ::: "memory");
         uint32_t bytes = 0;
         for (int dz = 0; dz < 3; ++dz) bytes += (uint32_t)((pr_hi[dz] - pr_lo[dz]) * WS * 4);
-        for (int dk = 0; dk < 2; ++dk) bytes += 3u * (uint32_t)((pl_hi[dk] - pl_lo[dk]) * WS * 4);
+        bytes += 3u * (uint32_t)((pl_hi[0] - pl_lo[0]) * WS * 4) + 2u * (uint32_t)((pl_hi[1] - pl_lo[1]) * WS * 4);
         mbar_expect_tx(bar, bytes);
         for (int dz = 0; dz < 3; ++dz) {
             if (pr_hi[dz] <= pr_lo[dz]) continue;
@@ -137,7 +138,7 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
             const uint32_t nb = (uint32_t)((pl_hi[dk] - pl_lo[dk]) * WS * 4);
             bulk_load(sPl + ((dk * 3 + 0) * (TY + 1) + pl_lo[dk]) * WS, s.X + row * WS, nb, bar);
             bulk_load(sPl + ((dk * 3 + 1) * (TY + 1) + pl_lo[dk]) * WS, s.Y + row * WS, nb, bar);
-            bulk_load(sPl + ((dk * 3 + 2) * (TY + 1) + pl_lo[dk]) * WS, s.Z + row * WS, nb, bar);
+            if (dk == 0) bulk_load(sPl + (2 * (TY + 1) + pl_lo[dk]) * WS, s.Z + row * WS, nb, bar);
         }
     }
     for (int slot = tid; slot < NS; slot += nthr) {
@@ -188,8 +189,8 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
             sF[(lr * 6 + f) * W + w] = F[f];
             deg += __popc(F[f]);
         }
-        sDpre[lr * W + w] = deg;
-        sQpre[lr * W + w] = __popc(Xa) + __popc(Ya) + __popc(Za);
+        sDpre[lr * W + w] = (uint16_t)deg;
+        sQpre[lr * W + w] = (uint16_t)(__popc(Xa) + __popc(Ya) + __popc(Za));
     }
     __syncthreads();
     // ---- per-row exclusive prefixes, one thread per row
@@ -197,146 +198,144 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
         int run = 0;
         if (r < NS) {
             for (int w = 0; w < W; ++w) {
-                sPre[r * W + w] = run;
+                sPre[r * W + w] = (uint16_t)run;
                 run += __popc(sP[r * WS + w]);
             }
         } else {
-            int32_t *a = r < NS + n ? sDpre + (r - NS) * W : sQpre + (r - NS - n) * W;
+            uint16_t *a = r < NS + n ? sDpre + (r - NS) * W : sQpre + (r - NS - n) * W;
             for (int w = 0; w < W; ++w) {
                 const int v = a[w];
-                a[w] = run;
+                a[w] = (uint16_t)run;
                 run += v;
             }
         }
     }
     __syncthreads();
 
-    // rank of cell bit p in staged row `slot`
-    auto rank = [&](int slot, int64_t p) -> int32_t {
-        const int w = (int)(p >> 5);
-        return sBase[slot] + sPre[slot * W + w] + __popc(sP[slot * WS + w] & ((1u << (p & 31)) - 1u));
+    // id of the point at cell bit p (word w, bits below it lt) of staged row `slot`
+    auto rank = [&](int slot, int w, uint32_t lt) -> int32_t {
+        return sBase[slot] + (int32_t)sPre[slot * W + w] + __popc(sP[slot * WS + w] & lt);
     };
 
-    // ---- points and stencils, in id order.  Thread k takes point pbase + k and
-    // finds its cell itself: the own row by a search of the row offsets, the
-    // word by a search of the row's per-word prefixes, the bit as the n-th set
-    // bit of that word.
+    // ---- points and stencils, in id order, chunk by chunk
     const int last = slot_of(1, n - 1);
     const int32_t pbase = sBase[slot_of(1, 0)];
-    const int32_t pend = sBase[last] + sPre[last * W + (W - 1)] + __popc(sP[last * WS + (W - 1)]);
-    for (int32_t id = pbase + tid; id < pend; id += nthr) {
-        int lr = 0;
-        for (int hi = n; hi - lr > 1;) { // the last own row whose first id is <= id
-            const int mid = (lr + hi) >> 1;
-            if (sBase[slot_of(1, mid)] <= id) lr = mid;
-            else hi = mid;
-        }
-        const int sr = slot_of(1, lr);
-        const int32_t r = id - sBase[sr];
-        int w = 0;
-        for (int hi = W; hi - w > 1;) { // the last word of the row with at most r points before it
-            const int mid = (w + hi) >> 1;
-            if (sPre[sr * W + mid] <= r) w = mid;
-            else hi = mid;
-        }
-        const int b = nth_bit(sP[sr * WS + w], r - sPre[sr * W + w]);
-        if (id < 0 || id >= NP) continue;
-        const uint32_t lt = (1u << b) - 1u;
-        const int64_t p = (int64_t)w * 32 + b;
-        const int64_t cx = p - 1, cy = c0 - 1 + lr;
-        float *pt = m.points + 3 * (int64_t)id;
-        pt[0] = m.lut_x[cx + 1].x;
-        pt[1] = m.lut_y[cy + 1].x;
-        pt[2] = m.lut_z[cz + 1].x;
-        float *of = m.offsets + 3 * (int64_t)id;
-        of[0] = 0.f;
-        of[1] = 0.f;
-        of[2] = 0.f;
-        m.cells[id] = (uint64_t)(cx + 1) | ((uint64_t)(cy + 1) << 21) | ((uint64_t)(cz + 1) << 42);
-        uint32_t mask = 0;
-        int64_t so = sSoff[lr] + sDpre[lr * W + w];
-#pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            const uint32_t fw = sF[(lr * 6 + f) * W + w];
-            so += __popc(fw & lt);
-            mask |= ((fw >> b) & 1u) << f;
-        }
-        m.face_mask[id] = (uint8_t)mask;
-        m.sten_off[id] = so;
-        if (so < 0 || so + __popc(mask) > NS_) continue;
-        int32_t *dst = m.sten_ids + so;
-        if (mask & 1u) *dst++ = id - 1;
-        if (mask & 2u) *dst++ = id + 1;
-        uint32_t dist[4] = {0u, 0u, 0u, 0u};
-        const int nbs[4] = {slot_of(1, lr - 1), slot_of(1, lr + 1), slot_of(0, lr), slot_of(2, lr)};
-#pragma unroll
-        for (int f = 2; f < 6; ++f)
-            if ((mask >> f) & 1u) {
-                const int32_t nb = rank(nbs[f - 2], p);
-                *dst++ = nb;
-                dist[f - 2] = (uint32_t)(nb > id ? nb - id : id - nb);
+    const int32_t npts = sBase[last] + (int32_t)sPre[last * W + (W - 1)] + __popc(sP[last * WS + (W - 1)]) - pbase;
+    for (int32_t lo = 0; lo < npts; lo += kListCap) {
+        const int32_t hi = npts - lo < kListCap ? npts : lo + kListCap;
+        __syncthreads(); // the previous chunk's list is read no more
+        for (int it = tid; it < n * W; it += nthr) {
+            const int lr = (int)(((uint64_t)(uint32_t)it * tg.wdiv) >> 32), w = it - lr * W;
+            const int sr = slot_of(1, lr);
+            uint32_t bits = sP[sr * WS + w];
+            int32_t t = sBase[sr] - pbase + (int32_t)sPre[sr * W + w];
+            if (!bits || t >= hi || t + __popc(bits) <= lo) continue;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                if (t >= lo && t < hi) sList[t - lo] = ((uint32_t)lr << 11) | (uint32_t)(w * 32 + b);
+                ++t;
             }
-        store_record(m, id, mask, dist);
+        }
+        __syncthreads();
+        for (int32_t k = lo + tid; k < hi; k += nthr) {
+            const uint32_t e = sList[k - lo];
+            const int lr = (int)(e >> 11), p = (int)(e & 2047u), w = p >> 5, b = p & 31;
+            const int32_t id = pbase + k;
+            if (id < 0 || id >= NP) continue;
+            const uint32_t lt = (1u << b) - 1u;
+            const int64_t cy = c0 - 1 + lr;
+            float *pt = m.points + 3 * (int64_t)id;
+            pt[0] = m.lut_x[p].x;
+            pt[1] = m.lut_y[cy + 1].x;
+            pt[2] = m.lut_z[czc].x;
+            m.cells[id] = (uint64_t)p | ((uint64_t)(cy + 1) << 21) | ((uint64_t)czc << 42);
+            uint32_t mask = 0;
+            int64_t so = sSoff[lr] + sDpre[lr * W + w];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                const uint32_t fw = sF[(lr * 6 + f) * W + w];
+                so += __popc(fw & lt);
+                mask |= ((fw >> b) & 1u) << f;
+            }
+            m.face_mask[id] = (uint8_t)mask;
+            m.sten_off[id] = so;
+            if (so < 0 || so + __popc(mask) > NS_) continue;
+            int32_t *dst = m.sten_ids + so;
+            if (mask & 1u) *dst++ = id - 1;
+            if (mask & 2u) *dst++ = id + 1;
+            uint32_t dist[4] = {0u, 0u, 0u, 0u};
+            const int nbs[4] = {slot_of(1, lr - 1), slot_of(1, lr + 1), slot_of(0, lr), slot_of(2, lr)};
+#pragma unroll
+            for (int f = 2; f < 6; ++f)
+                if ((mask >> f) & 1u) {
+                    const int32_t nb = rank(nbs[f - 2], w, lt);
+                    *dst++ = nb;
+                    dist[f - 2] = (uint32_t)(nb > id ? nb - id : id - nb);
+                }
+            store_record(m, id, mask, dist);
+        }
     }
 
     // ---- quads of sample rows (cy, cz), cy = c0 - 1 + lr, in quad order: within
-    // a word by bit, and at one bit x before y before z.  Thread k takes quad
-    // qbase + k and finds its row, word, bit and axis by searches as above.
+    // a word by bit, and at one bit x before y before z
     const int lr_first = (c0 == 0) ? 1 : 0; // cy = -1 has no sample row
     if (cz < 0 || lr_first >= n) return true;
     const int64_t qbase = sQoff[lr_first];
-    const int64_t qend = sQoff[n - 1] + sQpre[(n - 1) * W + (W - 1)] + __popc(PL(0, 0, n - 1)[W - 1]) +
-                         __popc(PL(0, 1, n - 1)[W - 1]) + __popc(PL(0, 2, n - 1)[W - 1]);
-    for (int64_t q = qbase + tid; q < qend; q += nthr) {
-        int lr = lr_first;
-        for (int hi = n; hi - lr > 1;) {
-            const int mid = (lr + hi) >> 1;
-            if (sQoff[mid] <= q) lr = mid;
-            else hi = mid;
-        }
-        const int32_t r = (int32_t)(q - sQoff[lr]);
-        int w = 0;
-        for (int hi = W; hi - w > 1;) {
-            const int mid = (w + hi) >> 1;
-            if (sQpre[lr * W + mid] <= r) w = mid;
-            else hi = mid;
-        }
-        const uint32_t qx = PL(0, 0, lr)[w], qy = PL(0, 1, lr)[w], qz = PL(0, 2, lr)[w];
-        const int rr = r - sQpre[lr * W + w];
-        int b = 0; // the last bit with at most rr quads of the word below it
+    const int32_t nqt = (int32_t)(sQoff[n - 1] - qbase) + (int32_t)sQpre[(n - 1) * W + (W - 1)] +
+                        __popc(PL(0, 0, n - 1)[W - 1]) + __popc(PL(0, 1, n - 1)[W - 1]) +
+                        __popc(PL(0, 2, n - 1)[W - 1]);
+    for (int32_t lo = 0; lo < nqt; lo += kListCap) {
+        const int32_t hi = nqt - lo < kListCap ? nqt : lo + kListCap;
+        __syncthreads();
+        for (int it = lr_first * W + tid; it < n * W; it += nthr) {
+            const int lr = (int)(((uint64_t)(uint32_t)it * tg.wdiv) >> 32), w = it - lr * W;
+            const uint32_t qx = PL(0, 0, lr)[w], qy = PL(0, 1, lr)[w], qz = PL(0, 2, lr)[w];
+            uint32_t bits = qx | qy | qz;
+            int32_t t = (int32_t)(sQoff[lr] - qbase) + (int32_t)sQpre[lr * W + w];
+            if (!bits || t >= hi || t + __popc(qx) + __popc(qy) + __popc(qz) <= lo) continue;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const uint32_t pos = ((uint32_t)lr << 13) | ((uint32_t)(w * 32 + b) << 2);
 #pragma unroll
-        for (int st = 16; st > 0; st >>= 1) {
-            const uint32_t mk = (1u << (b + st)) - 1u;
-            if (__popc(qx & mk) + __popc(qy & mk) + __popc(qz & mk) <= rr) b += st;
+                for (int ax = 0; ax < 3; ++ax)
+                    if ((((ax == 0 ? qx : ax == 1 ? qy : qz) >> b) & 1u)) {
+                        if (t >= lo && t < hi) sList[t - lo] = pos | (uint32_t)ax;
+                        ++t;
+                    }
+            }
         }
-        const uint32_t below = (1u << b) - 1u;
-        int k = rr - (__popc(qx & below) + __popc(qy & below) + __popc(qz & below));
-        const int hx = (int)((qx >> b) & 1u), hy = (int)((qy >> b) & 1u);
-        int ax = 2;
-        if (hx && k == 0) ax = 0;
-        else if (hy && k - hx == 0) ax = 1;
-        if (q < 0 || q >= NQ) continue;
-        const int64_t i = (int64_t)w * 32 + b;
-        const int64_t j = c0 - 1 + lr;
-        const T *row = lab + (j + ny * cz) * g.lp;
-        // cell rows: 00 = (cy, cz), m0 = (cy-1, cz), 0m = (cy, cz-1), mm = (cy-1, cz-1)
-        const int s00 = slot_of(1, lr), sm0 = slot_of(1, lr - 1), s0m = slot_of(0, lr), smm = slot_of(0, lr - 1);
-        int4 v;
-        int64_t d1;
-        if (ax == 0) {
-            v = make_int4(rank(smm, i + 1), rank(s0m, i + 1), rank(s00, i + 1), rank(sm0, i + 1));
-            d1 = 1;
-        } else if (ax == 1) {
-            v = make_int4(rank(s0m, i), rank(s00, i), rank(s00, i + 1), rank(s0m, i + 1));
-            d1 = g.lp;
-        } else {
-            v = make_int4(rank(sm0, i), rank(sm0, i + 1), rank(s00, i + 1), rank(s00, i));
-            d1 = g.lp * ny;
+        __syncthreads();
+        for (int32_t k = lo + tid; k < hi; k += nthr) {
+            const uint32_t e = sList[k - lo];
+            const int lr = (int)(e >> 13), i = (int)((e >> 2) & 2047u), ax = (int)(e & 3u);
+            const int64_t q = qbase + k;
+            if (q < 0 || q >= NQ) continue;
+            const int64_t j = c0 - 1 + lr;
+            const T *row = lab + (j + ny * cz) * g.lp;
+            // cell rows: 00 = (cy, cz), m0 = (cy-1, cz), 0m = (cy, cz-1), mm = (cy-1, cz-1)
+            const int s00 = slot_of(1, lr), sm0 = slot_of(1, lr - 1), s0m = slot_of(0, lr), smm = slot_of(0, lr - 1);
+            // cell bits i (cx = i - 1) and i + 1 (cx = i)
+            const int w0 = i >> 5, w1 = (i + 1) >> 5;
+            const uint32_t lt0 = (1u << (i & 31)) - 1u, lt1 = (1u << ((i + 1) & 31)) - 1u;
+            int4 v;
+            int64_t d1;
+            if (ax == 0) {
+                v = make_int4(rank(smm, w1, lt1), rank(s0m, w1, lt1), rank(s00, w1, lt1), rank(sm0, w1, lt1));
+                d1 = 1;
+            } else if (ax == 1) {
+                v = make_int4(rank(s0m, w0, lt0), rank(s00, w0, lt0), rank(s00, w1, lt1), rank(s0m, w1, lt1));
+                d1 = g.lp;
+            } else {
+                v = make_int4(rank(sm0, w0, lt0), rank(sm0, w1, lt1), rank(s00, w1, lt1), rank(s00, w0, lt0));
+                d1 = g.lp * ny;
+            }
+            reinterpret_cast<int4 *>(m.quads)[q] = v;
+            T *ql = reinterpret_cast<T *>(m.quad_labels) + 2 * q;
+            ql[0] = (T)kappa<MODE>(c, ldlab(row, i));
+            ql[1] = (T)kappa<MODE>(c, ldlab(row, i + d1));
         }
-        reinterpret_cast<int4 *>(m.quads)[q] = v;
-        T *ql = reinterpret_cast<T *>(m.quad_labels) + 2 * q;
-        ql[0] = (T)kappa<MODE>(c, ldlab(row, i));
-        ql[1] = (T)kappa<MODE>(c, ldlab(row, i + d1));
     }
     return true;
 }

@@ -284,10 +284,6 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 3) k_emit(const T *__restrict
             pt[0] = m.lut_x[cx + 1].x;
             pt[1] = m.lut_y[cy + 1].x;
             pt[2] = m.lut_z[cz + 1].x;
-            float *of = m.offsets + 3 * id64;
-            of[0] = 0.f;
-            of[1] = 0.f;
-            of[2] = 0.f;
             m.cells[id] = (uint64_t)(cx + 1) | ((uint64_t)(cy + 1) << 21) | ((uint64_t)(cz + 1) << 42);
             uint32_t mask = 0;
             int64_t so = sbase + sh.dpre[wp][wl];
@@ -632,10 +628,23 @@ cudaError_t launch_scan(const Geometry &g, const ExtractScratch &s, DevTotals *t
     return cudaGetLastError();
 }
 
-int rec_mode(const DevTotals &t)
+// the fewest bits that hold every id distance d < reach (d >= 1; at least one bit)
+static int bits_for(int64_t reach)
 {
-    if (t.yreach >= kPackedReach) return REC_CSR;
-    return t.zreach < kPackedReach ? REC_COMPACT : REC_WIDE;
+    const int64_t dmax = reach > 2 ? reach - 1 : 1;
+    int b = 0;
+    while (b < 62 && (1ll << b) <= dmax) ++b;
+    return b;
+}
+
+int rec_mode(const DevTotals &t, int *by, int *bz)
+{
+    *by = bits_for(t.yreach);
+    *bz = bits_for(t.zreach);
+    if (2 + 2 * *by + 2 * *bz <= 64) return REC_PACKED;
+    *by = 15;
+    *bz = 32;
+    return t.yreach <= kPackedReach ? REC_WIDE : REC_CSR;
 }
 
 cudaError_t launch_emit(int type, const void *labels, const Classifier &c, const Geometry &g,

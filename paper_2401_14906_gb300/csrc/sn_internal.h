@@ -70,11 +70,16 @@ struct DevTotals {
 
 // How the smoothing sweeps find a point's neighbours (chosen per mesh from the
 // totals' reach bounds, before the emission writes the records).
-enum RecMode {
-    REC_COMPACT = 0, // nbr: 15-bit -y/+y and -z/+z distances (8 bytes per point)
-    REC_WIDE = 1,    // nbr: 15-bit -y/+y distances and the 32-bit -z distance, nbrp: the +z distance (12 bytes)
-    REC_CSR = 2,     // the CSR stencil (-y/+y distances beyond 15 bits: rows wider than 16382 samples)
-};
+//   REC_PACKED: one 64-bit record per point (nbr as uint2 = low, high word):
+//       bit 0 / 1 = -x / +x neighbour present, then the |id distance| to the
+//       -y, +y neighbours in `by` bits each and to the -z, +z neighbours in
+//       `bz` bits each (0 = absent), by and bz the fewest bits that hold every
+//       distance the reach bounds allow; used while 2 + 2 by + 2 bz <= 64.
+//   REC_WIDE: nbr.x = the -x/+x bits and 15-bit -y/+y distances in the same
+//       order (by = 15), nbr.y = the 32-bit -z distance, nbrp = the +z distance
+//       (12 bytes per point); used when the -y/+y distances fit 15 bits.
+//   REC_CSR: the sweeps read the CSR stencil (rows of more than ~16k points).
+enum RecMode { REC_PACKED = 0, REC_WIDE = 1, REC_CSR = 2 };
 
 // Output arrays of a mesh.
 struct MeshArrays {
@@ -89,12 +94,10 @@ struct MeshArrays {
     int32_t *meta;       // [4]: 1 = smoothing error flag (0, 2 and 3 are unused)
     float2 *lut_x, *lut_y, *lut_z; // [n+1] cell-centre world coordinate per axis for c = -1..n-1, as
                                    // (hi, lo): hi = the coordinate rounded to float, lo = the rest
-    uint2 *nbr;          // [np] neighbour record for the smoothing sweeps (REC_COMPACT / REC_WIDE):
-                         //   .x = d(-y) | d(+y) << 16, each a 15-bit |id distance|, 0 = no neighbour, and
-                         //        bit 15 / 31 = -x / +x neighbour present;
-                         //   .y = d(-z) | d(+z) << 16 (15 bits each; REC_COMPACT) or d(-z) (REC_WIDE)
+    uint2 *nbr;          // [np] neighbour record for the smoothing sweeps (REC_PACKED / REC_WIDE, see RecMode)
     uint32_t *nbrp;      // [np] d(+z) (REC_WIDE only)
     int rec;             // RecMode of this mesh
+    int by, bz;          // REC_PACKED field widths
 };
 
 constexpr int32_t kPackedReach = 1 << 15; // packed records hold id distances below this
@@ -160,8 +163,8 @@ cudaError_t launch_count_range(int type, const void *labels, const Classifier &c
 // clear = false: the scan flags and ticket are already zero
 cudaError_t launch_scan(const Geometry &g, const ExtractScratch &s, DevTotals *totals, cudaStream_t st,
                         bool clear = true);
-// record mode for a mesh whose totals are `t`
-int rec_mode(const DevTotals &t);
+// record mode (and REC_PACKED field widths) for a mesh whose totals are `t`
+int rec_mode(const DevTotals &t, int *by, int *bz);
 cudaError_t launch_emit(int type, const void *labels, const Classifier &c, const Geometry &g,
                         const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st);
 

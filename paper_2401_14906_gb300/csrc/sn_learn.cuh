@@ -27,6 +27,7 @@ __device__ __forceinline__ float3 unit_sum(uint32_t fm)
 
 // First loads of a point's features (its face mask and either its packed
 // neighbour record or its stencil offset), issued a tile ahead by the proposal.
+// `packed`: the mesh's records are REC_PACKED (else the CSR stencil is read).
 struct FeatPre {
     uint32_t fm;
     uint2 r;
@@ -49,8 +50,8 @@ __device__ __forceinline__ FeatPre feature_loads(const MeshArrays &m, int64_t i,
 
 // The 32 BF16 feature slots of point i, two lanes per point: half 0 writes
 // slots 0..9, 28..31 and the neighbour blocks of faces 0-2, half 1 the blocks
-// of faces 3-5.  Neighbour ids come from the packed record while every id
-// distance fits it, else from the CSR stencil.
+// of faces 3-5.  Neighbour ids come from the 8-byte record when the mesh has
+// one, else from the CSR stencil.
 __device__ __forceinline__ void point_features(const MeshArrays &m, int64_t i, int half, uint16_t hbits, bool packed,
                                                const FeatPre &p, uint16_t *row)
 {
@@ -68,14 +69,15 @@ __device__ __forceinline__ void point_features(const MeshArrays &m, int64_t i, i
     }
     int64_t nb[3];
     if (packed) {
+        const dev::NbrDist d = dev::decode_record(p.r, 0u, REC_PACKED, m.by, m.bz);
         if (half == 0) {
             nb[0] = i - 1;
             nb[1] = i + 1;
-            nb[2] = i - (int64_t)(p.r.x & 0x7fffu);
+            nb[2] = i - (int64_t)d.dmy;
         } else {
-            nb[0] = i + (int64_t)((p.r.x >> 16) & 0x7fffu);
-            nb[1] = i - (int64_t)(p.r.y & 0xffffu);
-            nb[2] = i + (int64_t)(p.r.y >> 16);
+            nb[0] = i + (int64_t)d.dpy;
+            nb[1] = i - (int64_t)d.dmz;
+            nb[2] = i + (int64_t)d.dpz;
         }
     } else {
         for (int q = 0; q < 3; ++q) {

@@ -48,6 +48,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_smooth_batch(const SmoothBatc
     a.nbr = mp.m.nbr;
     a.nbrp = mp.m.nbrp;
     a.rec = mp.m.rec;
+    a.by = mp.m.by;
+    a.bz = mp.m.bz;
     a.soff = mp.m.sten_off;
     a.sids = mp.m.sten_ids;
     a.fmask = mp.m.face_mask;
@@ -124,6 +126,8 @@ cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float
     a.nbr = m.nbr;
     a.nbrp = m.nbrp;
     a.rec = m.rec;
+    a.by = m.by;
+    a.bz = m.bz;
     a.soff = m.sten_off;
     a.sids = m.sten_ids;
     a.fmask = m.face_mask;
@@ -181,6 +185,8 @@ cudaError_t launch_smooth_from(const MeshArrays &m, int64_t np, int iterations, 
     a.nbr = m.nbr;
     a.nbrp = m.nbrp;
     a.rec = m.rec;
+    a.by = m.by;
+    a.bz = m.bz;
     a.soff = m.sten_off;
     a.sids = m.sten_ids;
     a.fmask = m.face_mask;

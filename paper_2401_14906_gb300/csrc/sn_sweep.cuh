@@ -11,17 +11,17 @@
 //
 // A point's neighbours come from a record written during extraction: the
 // -x/+x neighbours are always id-1/id+1 (one presence bit each), and the
-// -y/+y/-z/+z neighbours are stored as id distances (0 = absent).  While every
-// distance fits 15 bits the record is 8 bytes (REC_COMPACT); meshes whose
-// slices hold too many points for that (the 1024^2 x 512 connectome-like map)
-// keep the -z/+z distances in 32 bits, 12 bytes per point (REC_WIDE: the -z
-// distance in the second word of the 8-byte record, the +z one in a separate
-// array).  Per point a sweep streams 12 B in + 12 B out + the record from HBM;
-// neighbours are gathered from L2 or L1.  Rows of more than 16382 samples,
-// whose -y/+y distances may not fit 15 bits, use the CSR stencil (REC_CSR).
+// -y/+y/-z/+z neighbours are stored as id distances (0 = absent).  The record
+// is 8 bytes whenever the distances allowed by the mesh's reach bounds fit 62
+// bits together (REC_PACKED, field widths per mesh: 11 + 11 bits for -y/+y
+// and 20 + 20 for -z/+z on the 1024^2 x 512 connectome-like map); else 12 bytes
+// (REC_WIDE, 32-bit -z/+z distances).  Per point a sweep streams 12 B in + 12 B
+// out + the record from HBM; neighbours are gathered from L2 or L1.  Rows of
+// more than ~16k points, whose -y/+y distances may not fit 15 bits, use the CSR
+// stencil (REC_CSR).
 #pragma once
 
-#include "sn_internal.h"
+#include "sn_device.cuh"
 
 namespace sn {
 namespace dev {
@@ -49,11 +49,7 @@ struct SweepArgs {
     int first, last; // first sweep: offsets are all zero; last sweep: also write world coordinates
     int sphere;      // constrain |o| <= h instead of |o_a| <= h per axis
     int rec;         // RecMode of the mesh
-};
-
-// A point's decoded record: -x/+x presence and the four id distances.
-struct Nbr {
-    uint32_t xy, dmz, dpz;
+    int by, bz;      // REC_PACKED field widths
 };
 
 // The constraint of Sec. 2.2: a box of half-width h per axis, or a ball of radius h.
@@ -85,11 +81,10 @@ template <bool COH> __device__ __forceinline__ float3 ld3(const float *__restric
 }
 
 // Neighbour sum and update of one point (neighbour record).
-template <bool COH> __device__ __forceinline__ void sweep_point(const SweepArgs &a, uint32_t i, float3 o, Nbr r)
+template <bool COH> __device__ __forceinline__ void sweep_point(const SweepArgs &a, uint32_t i, float3 o, NbrDist r)
 {
     const float *__restrict__ oin = a.oin;
-    const uint32_t mx = (r.xy >> 15) & 1u, px = r.xy >> 31;
-    const uint32_t dmy = r.xy & 0x7fffu, dpy = (r.xy >> 16) & 0x7fffu, dmz = r.dmz, dpz = r.dpz;
+    const uint32_t mx = r.mx, px = r.px, dmy = r.dmy, dpy = r.dpy, dmz = r.dmz, dpz = r.dpz;
     const int n = (int)(mx + px + (dmy != 0) + (dpy != 0) + (dmz != 0) + (dpz != 0));
     float3 acc = make_float3((float)((int)px - (int)mx), (float)((int)(dpy != 0) - (int)(dmy != 0)),
                              (float)((int)(dpz != 0) - (int)(dmz != 0)));
@@ -187,20 +182,14 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, uint32_t base)
         return;
     }
     float3 o[PPT];
-    Nbr r[PPT];
+    NbrDist r[PPT];
     const bool wide = a.rec == REC_WIDE;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         const uint32_t i = base + threadIdx.x + q * kSweepThreads;
         const uint2 v = i < np ? a.nbr[i] : make_uint2(0u, 0u);
-        r[q].xy = v.x;
-        if (wide) {
-            r[q].dmz = v.y;
-            r[q].dpz = i < np ? a.nbrp[i] : 0u;
-        } else {
-            r[q].dmz = v.y & 0xffffu;
-            r[q].dpz = v.y >> 16;
-        }
+        const uint32_t p = (wide && i < np) ? a.nbrp[i] : 0u;
+        r[q] = decode_record(v, p, a.rec, a.by, a.bz);
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
 #pragma unroll

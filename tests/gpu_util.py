@@ -15,7 +15,7 @@ OFFSET_TOL = 1e-5
 
 
 def run_gpu(labels, spacing=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0), selected=None, background=0, iterations=16,
-            relaxation=0.5, constraint=1.0, on_device=True, sphere=False, triangulate=None):
+            relaxation=0.5, constraint=1.0, on_device=True, sphere=False, triangulate=None, record_bytes=None):
     import torch
 
     from paper_2401_14906_gb300 import sn
@@ -32,6 +32,8 @@ def run_gpu(labels, spacing=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0), selected=No
         src = np.ascontiguousarray(labels)
     if on_device != "uploaded":
         m = sn.sn_extract(src, spacing, origin, selected=selected, background=background)
+    if record_bytes is not None:
+        assert sn.sn_mesh_record_bytes(m) == record_bytes
     ext = sn.sn_mesh_copy_to_host(m)
     ext["face_masks"] = sn.sn_mesh_face_masks_host(m)
     smo = None
@@ -99,9 +101,9 @@ def compare_triangles(gpu_tris, quads, ref_tris, ref_alt, ref_metric, exact):
 
 
 def parity(labels, spacing=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0), selected=None, background=0, iterations=16,
-           relaxation=0.5, constraint=1.0, on_device=True, sphere=False, triangulate=None):
+           relaxation=0.5, constraint=1.0, on_device=True, sphere=False, triangulate=None, record_bytes=None):
     gpu_e, gpu_s = run_gpu(labels, spacing, origin, selected, background, iterations, relaxation, constraint,
-                           on_device, sphere, triangulate)
+                           on_device, sphere, triangulate, record_bytes)
     ref = oracle.extract(labels, spacing, origin, selected, background)
     compare_extract(gpu_e, ref)
     if iterations is not None:

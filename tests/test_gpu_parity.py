@@ -140,27 +140,19 @@ def _record_bytes(lab):
     return b
 
 
-def test_wide_slices_use_the_wide_record():
-    # a checkerboard with 261x261 cells per slice: -z/+z neighbours are ~68k ids
-    # apart, beyond the 15-bit fields of the 8-byte record, so the sweeps read
-    # 32-bit -z/+z distances (12-byte record)
-    z, y, x = np.mgrid[0:3, 0:260, 0:260]
-    lab = ((x + y + z) % 2).astype(np.uint8)
-    assert _record_bytes(lab) == 12
-    parity(lab, iterations=6)
-    # and a map below the limit in the same run of tests
-    z, y, x = np.mgrid[0:3, 0:120, 0:120]
-    lab = ((x + y + z) % 2).astype(np.uint8)
-    assert _record_bytes(lab) == 8
-    parity(lab, iterations=6)
-
-
-def test_very_wide_dense_rows_use_the_stencil():
-    # 20,000 samples per row alternating between two labels: every cell row holds
-    # ~20k points, so -y/+y distances may exceed 15 bits and the sweeps read the CSR
-    z, y, x = np.mgrid[0:3, 0:3, 0:20000]
+@pytest.mark.parametrize("shape,want", [
+    ((3, 120, 120), 8),    # small fields
+    ((3, 260, 260), 8),    # -z/+z distances of ~68k ids: 18-bit z fields, 10-bit y fields
+    ((3, 200, 2000), 12),  # ~400k points per slice and ~2k per row: 2 + 2*12 + 2*20 > 64 bits (tiled emission)
+    ((3, 2, 16000), 12),   # rows of ~16k points: 15-bit y fields (per-row emission)
+    ((3, 3, 20000), 0),    # rows of ~20k points: -y/+y distances beyond 15 bits, the sweeps read the CSR
+])
+def test_sweep_record_widths(shape, want):
+    """Checkerboards whose point density fixes the sweep record: 8 bytes with per-mesh field widths,
+    12 bytes with 32-bit -z/+z distances, or the CSR stencil."""
+    z, y, x = np.mgrid[0:shape[0], 0:shape[1], 0:shape[2]]
     lab = ((x + y + z) % 2).astype(np.uint16)
-    assert _record_bytes(lab) == 0
+    assert _record_bytes(lab) == want
     parity(lab, iterations=5)
 
 
@@ -231,12 +223,11 @@ def test_config2_full_size():
 
 def test_config3_full_size():
     # 1024x1024x512 uint32, 50,000 Voronoi cells with (1,1,4) spacing and 5% gaps:
-    # ~1.4e8 points, whose -z/+z neighbours are beyond the 15-bit fields, so the
-    # sweeps read the 12-byte record at full size
+    # ~1.4e8 points; the sweep record packs 11-bit -y/+y and 20-bit -z/+z
+    # distances into 8 bytes
     w = sn_synth.config3()
-    assert _record_bytes(w.labels[:64]) == 12
     ref = parity(w.labels, w.spacing, w.origin, iterations=w.iterations, relaxation=w.relaxation,
-                 constraint=w.constraint)
+                 constraint=w.constraint, record_bytes=8)
     assert ref.n_points > 100_000_000
 
 
