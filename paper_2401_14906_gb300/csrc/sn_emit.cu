@@ -17,14 +17,21 @@
 // searches of the row offsets, the row's per-word prefixes and the word's bits.
 #include "sn_emit_tile.cuh"
 
+// threads per tile (compile-time; tiles of kTileRows cell rows, sn_emit_tile.cuh)
+#ifndef SN_EMIT_THREADS
+#define SN_EMIT_THREADS 256
+#endif
+
 namespace sn {
 
 namespace {
 
 using namespace dev;
 
+constexpr int kEmitThreads = SN_EMIT_THREADS;
+
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_emit_tile(const T *__restrict__ lab, Classifier c, Geometry g,
+__global__ void __launch_bounds__(kEmitThreads) k_emit_tile(const T *__restrict__ lab, Classifier c, Geometry g,
                                                    ExtractScratch s, MeshArrays m, DevTotals *tot, TileGeom tg)
 {
     emit_tile<T, MODE>(lab, c, g, s, m, tot, tg, blockIdx.x, blockIdx.y);
@@ -42,7 +49,7 @@ cudaError_t emit_tile_t(const void *labels, const Classifier &c, const Geometry 
     cudaError_t e = smem_limit_once(k_emit_tile<T, MODE>, kMaxSmem, done);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((g.ny + 1 + tg.ty - 1) / tg.ty), (unsigned)(g.nz + 1));
-    k_emit_tile<T, MODE><<<grid, 256, smem, st>>>((const T *)labels, c, g, s, m, tot, tg);
+    k_emit_tile<T, MODE><<<grid, kEmitThreads, smem, st>>>((const T *)labels, c, g, s, m, tot, tg);
     return cudaGetLastError();
 }
 

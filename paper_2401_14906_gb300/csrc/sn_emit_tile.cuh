@@ -8,13 +8,16 @@
 namespace sn {
 namespace dev {
 
-constexpr int kTileRows = 24;  // cell rows per tile of the single-map kernel
+#ifndef SN_EMIT_ROWS
+#define SN_EMIT_ROWS 24
+#endif
+constexpr int kTileRows = SN_EMIT_ROWS; // cell rows per tile of the single-map kernel
 constexpr int kTileMaxW = 64;  // rows of up to 2047 cells; wider rows use the per-row kernel
 constexpr int kListCap = 2048; // entries of the tile's position list (one chunk of points or quads)
 
 // shared-memory carve-up, in 4-byte words; every array starts on 16 bytes
 struct TileSmem {
-    int bar, P, planes, pre, base, F, dpre, qpre, soff, qoff, list, total;
+    int bar, P, planes, wb, F, dpre, qpre, soff, qoff, list, total;
     __host__ __device__ static int up4(int v) { return (v + 3) & ~3; }
     __host__ __device__ TileSmem(int ty, int W, int WS)
     {
@@ -22,9 +25,8 @@ struct TileSmem {
         bar = 0;                               // one mbarrier, padded to 16 bytes
         P = 4;                                 // [ns][WS] point-plane words
         planes = P + ns * WS;                  // [5 plane][ty+1 rows][WS]: X, Y, Z of slice cz, X, Y of cz+1
-        pre = planes + 5 * (ty + 1) * WS;      // [ns][W] uint16 points before the word, within the row
-        base = pre + up4((ns * W + 1) / 2);    // [ns] first point id of the row
-        F = base + up4(ns);                    // [ty][6][W] face planes of own rows
+        wb = planes + 5 * (ty + 1) * WS;       // [ns][W] id of the first point of the word (int32)
+        F = wb + up4(ns * W);                  // [ty][6][W] face planes of own rows
         dpre = F + up4(ty * 6 * W);            // [ty][W] uint16 stencil entries before the word
         qpre = dpre + up4((ty * W + 1) / 2);   // [ty][W] uint16 quads before the word
         soff = qpre + up4((ty * W + 1) / 2);   // [ty] int64 first stencil entry of the row
@@ -44,9 +46,10 @@ struct TileSmem {
 // order in chunks of kListCap: for each chunk, one thread per (row, word)
 // lists the positions of the word's points that fall in the chunk (a loop over
 // the word's set bits), and then one thread per id takes its position from the
-// list -- consecutive threads write consecutive ids.  Within-row prefixes
-// (points, stencil entries and quads before each word) are uint16: a row holds
-// at most 2048 cells.
+// list -- consecutive threads write consecutive ids.  A point's id, and the id
+// of a neighbour in a staged row, is the id of the first point of its word plus
+// the set bits below it.  Within-row prefixes of stencil entries and quads are
+// uint16: a row holds at most 2048 cells.
 template <typename T, int MODE>
 __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Classifier &c, const Geometry &g,
                                           const ExtractScratch &s, const MeshArrays &m, DevTotals *tot,
@@ -64,8 +67,7 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.bar);
     uint32_t *sP = sm + L.P;
     uint32_t *sPl = sm + L.planes;
-    uint16_t *sPre = reinterpret_cast<uint16_t *>(sm + L.pre);
-    int32_t *sBase = reinterpret_cast<int32_t *>(sm + L.base);
+    int32_t *sWB = reinterpret_cast<int32_t *>(sm + L.wb);
     uint32_t *sF = sm + L.F;
     uint16_t *sDpre = reinterpret_cast<uint16_t *>(sm + L.dpre);
     uint16_t *sQpre = reinterpret_cast<uint16_t *>(sm + L.qpre);
@@ -141,10 +143,6 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
             if (dk == 0) bulk_load(sPl + (2 * (TY + 1) + pl_lo[dk]) * WS, s.Z + row * WS, nb, bar);
         }
     }
-    for (int slot = tid; slot < NS; slot += nthr) {
-        const int dz = slot / (TY + 2), lr = slot - dz * (TY + 2) - 1;
-        sBase[slot] = (lr >= pr_lo[dz] && lr < pr_hi[dz]) ? (int32_t)__ldcg(s.offP + c0 + lr + ny1 * (czc - 1 + dz)) : 0;
-    }
     for (int lr = tid; lr < n; lr += nthr) {
         const int64_t cy = c0 - 1 + lr;
         sSoff[lr] = __ldcg(s.offS + rc0 + lr);
@@ -193,15 +191,19 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
         sQpre[lr * W + w] = (uint16_t)(__popc(Xa) + __popc(Ya) + __popc(Za));
     }
     __syncthreads();
-    // ---- per-row exclusive prefixes, one thread per row
+    // ---- per-row exclusive prefixes, one thread per row: first point id of each
+    // word of the staged point-plane rows, stencil entries and quads before each
+    // word of the own rows
     for (int r = tid; r < NS + 2 * n; r += nthr) {
-        int run = 0;
         if (r < NS) {
+            const int dz = r / (TY + 2), lr = r - dz * (TY + 2) - 1;
+            int32_t run = (lr >= pr_lo[dz] && lr < pr_hi[dz]) ? (int32_t)__ldcg(s.offP + c0 + lr + ny1 * (czc - 1 + dz)) : 0;
             for (int w = 0; w < W; ++w) {
-                sPre[r * W + w] = (uint16_t)run;
+                sWB[r * W + w] = run;
                 run += __popc(sP[r * WS + w]);
             }
         } else {
+            int run = 0;
             uint16_t *a = r < NS + n ? sDpre + (r - NS) * W : sQpre + (r - NS - n) * W;
             for (int w = 0; w < W; ++w) {
                 const int v = a[w];
@@ -214,13 +216,13 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
 
     // id of the point at cell bit p (word w, bits below it lt) of staged row `slot`
     auto rank = [&](int slot, int w, uint32_t lt) -> int32_t {
-        return sBase[slot] + (int32_t)sPre[slot * W + w] + __popc(sP[slot * WS + w] & lt);
+        return sWB[slot * W + w] + __popc(sP[slot * WS + w] & lt);
     };
 
     // ---- points and stencils, in id order, chunk by chunk
     const int last = slot_of(1, n - 1);
-    const int32_t pbase = sBase[slot_of(1, 0)];
-    const int32_t npts = sBase[last] + (int32_t)sPre[last * W + (W - 1)] + __popc(sP[last * WS + (W - 1)]) - pbase;
+    const int32_t pbase = sWB[slot_of(1, 0) * W];
+    const int32_t npts = sWB[last * W + (W - 1)] + __popc(sP[last * WS + (W - 1)]) - pbase;
     for (int32_t lo = 0; lo < npts; lo += kListCap) {
         const int32_t hi = npts - lo < kListCap ? npts : lo + kListCap;
         __syncthreads(); // the previous chunk's list is read no more
@@ -228,7 +230,7 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
             const int lr = (int)(((uint64_t)(uint32_t)it * tg.wdiv) >> 32), w = it - lr * W;
             const int sr = slot_of(1, lr);
             uint32_t bits = sP[sr * WS + w];
-            int32_t t = sBase[sr] - pbase + (int32_t)sPre[sr * W + w];
+            int32_t t = sWB[sr * W + w] - pbase;
             if (!bits || t >= hi || t + __popc(bits) <= lo) continue;
             while (bits) {
                 const int b = __ffs(bits) - 1;

@@ -153,7 +153,14 @@ template <bool COH> __device__ __forceinline__ void sweep_point_csr(const SweepA
     }
 }
 
-constexpr int kSweepThreads = 256, kSweepPoints = 2 * kSweepThreads; // two points per thread
+#ifndef SN_SWEEP_THREADS
+#define SN_SWEEP_THREADS 256
+#endif
+#ifndef SN_SWEEP_PPT
+#define SN_SWEEP_PPT 2
+#endif
+constexpr int kSweepPPT = SN_SWEEP_PPT; // points per thread
+constexpr int kSweepThreads = SN_SWEEP_THREADS, kSweepPoints = kSweepPPT * kSweepThreads;
 
 // Points [base, base + PPT * kSweepThreads) of one Jacobi sweep.  Each thread
 // updates PPT points kSweepThreads apart; the own offsets and neighbour records
@@ -167,7 +174,7 @@ constexpr int kSweepThreads = 256, kSweepPoints = 2 * kSweepThreads; // two poin
 // and only then waits for the previous sweep to finish before it reads or
 // writes any offsets.  A launch without that attribute returns from the wait
 // at once.
-template <bool COH, int PPT = 2>
+template <bool COH, int PPT = kSweepPPT>
 __device__ __forceinline__ void sweep_block(const SweepArgs &a, uint32_t base)
 {
     const uint64_t np = (uint64_t)a.np;
