@@ -34,9 +34,10 @@ struct sn_mesh {
     cudaEvent_t copied;    // the last sn_mesh_copy_to_host_async has finished
     int32_t *copy_meta;    // its copy of the meta words (pinned)
     bool copy_pending;
-    // The extraction does not write the offsets (a smoothing overwrites them all);
-    // until something does, they are zeroed when first handed out (ensure_offsets).
-    bool offsets_pending;
+    // The extraction writes neither the world positions nor the offsets (a
+    // smoothing writes them all); until something does, they are set to the cell
+    // centres and zero when first handed out (ensure_centres).
+    bool centres_pending;
 };
 
 // A label map copied to the device ahead of its extraction (sn_labels_upload).
@@ -171,14 +172,15 @@ std::map<std::string, ProfEntry> g_prof;
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
-// Zeroes a mesh's offsets on its stream if nothing has written them yet (an
-// extraction that no smoothing followed): the state in which they are handed out.
-cudaError_t ensure_offsets(const sn_mesh *cm)
+// Writes a mesh's world positions (the cell centres) and zero offsets on its
+// stream if nothing has written them yet (an extraction that no smoothing
+// followed): the state in which they are handed out.
+cudaError_t ensure_centres(const sn_mesh *cm)
 {
     sn_mesh *m = const_cast<sn_mesh *>(cm);
-    if (!m->offsets_pending || m->np == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(m->a.offsets, 0, sizeof(float) * 3 * (size_t)m->np, m->stream);
-    if (e == cudaSuccess) m->offsets_pending = false;
+    if (!m->centres_pending || m->np == 0) return cudaSuccess;
+    cudaError_t e = sn::launch_centres(m->a, m->np, m->stream);
+    if (e == cudaSuccess) m->centres_pending = false;
     return e;
 }
 
@@ -594,7 +596,7 @@ sn_status job_allocate(ExtractJob &j, cudaStream_t st, bool with_smooth_buffer =
     }
     if (smooth_bytes) m->smooth_scratch = reinterpret_cast<float *>(block);
     if (m->a.rec != sn::REC_WIDE) m->a.nbrp = nullptr; // (given no bytes above)
-    m->offsets_pending = true;
+    m->centres_pending = true;
     m->a.lut_y = m->a.lut_x + (nx + 1);
     m->a.lut_z = m->a.lut_y + (ny + 1);
     j.mesh = m;
@@ -853,7 +855,7 @@ sn_status sn_smooth_ex(sn_mesh *m, int iterations, float relaxation, float const
     cudaError_t e = sn::launch_smooth(m->a, m->np, iterations, relaxation, 0.5f * constraint_distance,
                                       constraint == SN_CONSTRAINT_SPHERE, m->smooth_scratch, m->spacing, m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "smoothing launch");
-    m->offsets_pending = false; // every offset is written
+    m->centres_pending = false; // every position and offset is written
     return SN_OK;
 }
 
@@ -867,7 +869,8 @@ sn_status sn_triangulate(sn_mesh *m, sn_tri_method method)
         sn_status r = pool_alloc((void **)&m->tris, sizeof(int32_t) * 6 * (size_t)m->nq, m->pool, m->stream, "triangles");
         if (r != SN_OK) return r;
     }
-    cudaError_t e = sn::launch_triangulate(m->a, m->np, m->nq, (int)method, m->tris, m->stream);
+    cudaError_t e = ensure_centres(m);
+    if (e == cudaSuccess) e = sn::launch_triangulate(m->a, m->np, m->nq, (int)method, m->tris, m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "triangulation launch");
     return SN_OK;
 }
@@ -893,9 +896,9 @@ sn_status sn_mesh_device_arrays(const sn_mesh *m, const float **points, const in
                                 const int32_t **stencil_ids, const float **offsets)
 {
     if (!m) return fail(SN_EINVAL, "mesh is NULL");
-    if (offsets) {
-        cudaError_t e = ensure_offsets(m);
-        if (e != cudaSuccess) return cuda_fail(e, "offsets");
+    if (points || offsets) {
+        cudaError_t e = ensure_centres(m);
+        if (e != cudaSuccess) return cuda_fail(e, "cell centres");
     }
     if (points) *points = m->a.points;
     if (quads) *quads = m->a.quads;
@@ -931,9 +934,9 @@ sn_status sn_mesh_copy_to_host(const sn_mesh *m, float *points, int32_t *quads, 
                                int64_t *stencil_offsets, int32_t *stencil_ids, float *offsets)
 {
     if (!m) return fail(SN_EINVAL, "mesh is NULL");
-    if (offsets) {
-        cudaError_t e0 = ensure_offsets(m);
-        if (e0 != cudaSuccess) return cuda_fail(e0, "offsets");
+    if (points || offsets) {
+        cudaError_t e0 = ensure_centres(m);
+        if (e0 != cudaSuccess) return cuda_fail(e0, "cell centres");
     }
     struct {
         void *dst;
@@ -1015,8 +1018,8 @@ sn_status sn_mesh_copy_to_host_async(sn_mesh *m, float *points, int32_t *quads, 
     cudaStream_t cs = d2h_stream(m->device);
     int32_t *meta = meta_slot();
     if (!cs || !meta) return fail(SN_ENOMEM, "copy stream or pinned meta slot");
-    cudaError_t e = offsets ? ensure_offsets(m) : cudaSuccess; // (on the mesh's stream, before `smoothed`)
-    if (e != cudaSuccess) return cuda_fail(e, "offsets");
+    cudaError_t e = (points || offsets) ? ensure_centres(m) : cudaSuccess; // (on the mesh's stream, before `smoothed`)
+    if (e != cudaSuccess) return cuda_fail(e, "cell centres");
     if (!m->copied && (e = cudaEventCreateWithFlags(&m->copied, cudaEventDisableTiming)) != cudaSuccess) {
         m->copied = nullptr;
         return cuda_fail(e, "copy event");
@@ -1212,7 +1215,7 @@ sn_status sn_learner_add_examples(sn_learner *l, const sn_mesh *m, float constra
         return fail(SN_EINVAL, "constraint distance must be finite and >= 0");
     if (m->np == 0) return SN_OK;
     // the mesh's work must be complete before the learner's stream reads it
-    cudaError_t e = ensure_offsets(m);
+    cudaError_t e = ensure_centres(m);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "mesh stream");
     const int64_t need = l->n + m->np;
@@ -1383,7 +1386,7 @@ sn_status sn_smooth_learned(sn_mesh *m, const sn_learner *l, int corrections, fl
         e = sn::launch_smooth_from(m->a, m->np, corrections, relaxation, half, sphere, start,
                                    start == m->a.offsets ? m->smooth_scratch : m->a.offsets, m->spacing, m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "learned smoothing launch");
-    m->offsets_pending = false; // every offset is written
+    m->centres_pending = false; // every position and offset is written
     return SN_OK;
 }
 
@@ -1748,7 +1751,7 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
     }
     for (int64_t i = 0; i < n_maps; ++i) {
         jobs[i].mesh->stream = st;
-        jobs[i].mesh->offsets_pending = iterations == 0; // else the sweeps wrote every offset
+        jobs[i].mesh->centres_pending = iterations == 0; // else the sweeps wrote every position and offset
         out[i] = jobs[i].mesh;
     }
     return finish(SN_OK);

@@ -17,7 +17,7 @@ constexpr int kListCap = 2048; // entries of the tile's position list (one chunk
 
 // shared-memory carve-up, in 4-byte words; every array starts on 16 bytes
 struct TileSmem {
-    int bar, P, planes, wb, F, dpre, qpre, soff, qoff, list, total;
+    int bar, P, planes, wb, dpre, qpre, soff, qoff, list, total;
     __host__ __device__ static int up4(int v) { return (v + 3) & ~3; }
     __host__ __device__ TileSmem(int ty, int W, int WS)
     {
@@ -26,8 +26,7 @@ struct TileSmem {
         P = 4;                                 // [ns][WS] point-plane words
         planes = P + ns * WS;                  // [5 plane][ty+1 rows][WS]: X, Y, Z of slice cz, X, Y of cz+1
         wb = planes + 5 * (ty + 1) * WS;       // [ns][W] id of the first point of the word (int32)
-        F = wb + up4(ns * W);                  // [ty][6][W] face planes of own rows
-        dpre = F + up4(ty * 6 * W);            // [ty][W] uint16 stencil entries before the word
+        dpre = wb + up4(ns * W);               // [ty][W] uint16 stencil entries before the word
         qpre = dpre + up4((ty * W + 1) / 2);   // [ty][W] uint16 quads before the word
         soff = qpre + up4((ty * W + 1) / 2);   // [ty] int64 first stencil entry of the row
         qoff = soff + 2 * ty;                  // [ty] int64 first quad of the sample row
@@ -46,7 +45,11 @@ struct TileSmem {
 // order in chunks of kListCap: for each chunk, one thread per (row, word)
 // lists the positions of the word's points that fall in the chunk (a loop over
 // the word's set bits), and then one thread per id takes its position from the
-// list -- consecutive threads write consecutive ids.  A point's id, and the id
+// list -- consecutive threads write consecutive ids.  The list entry of a point
+// also carries its face mask and the stencil entries of the points before it in
+// its word, which the listing thread derives from the word's face planes.  The
+// world positions are not written here: the smoothing writes them, and a mesh
+// handed out unsmoothed gets its cell centres then.  A point's id, and the id
 // of a neighbour in a staged row, is the id of the first point of its word plus
 // the set bits below it.  Within-row prefixes of stencil entries and quads are
 // uint16: a row holds at most 2048 cells.
@@ -68,7 +71,6 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
     uint32_t *sP = sm + L.P;
     uint32_t *sPl = sm + L.planes;
     int32_t *sWB = reinterpret_cast<int32_t *>(sm + L.wb);
-    uint32_t *sF = sm + L.F;
     uint16_t *sDpre = reinterpret_cast<uint16_t *>(sm + L.dpre);
     uint16_t *sQpre = reinterpret_cast<uint16_t *>(sm + L.qpre);
     int64_t *sSoff = reinterpret_cast<int64_t *>(sm + L.soff);
@@ -156,10 +158,11 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
     auto PL = [&](int dk, int p, int lr) -> const uint32_t * { return sPl + ((dk * 3 + p) * (TY + 1) + lr) * WS; };
     auto slot_of = [&](int dz, int lr) { return dz * (TY + 2) + lr + 1; };
 
-    // ---- face planes of own cell rows, one thread per word
-    for (int it = tid; it < n * W; it += nthr) {
-        const int lr = (int)(((uint64_t)(uint32_t)it * tg.wdiv) >> 32), w = it - lr * W;
-        // sample rows a = (lr, dk0), b = (lr+1, dk0), c = (lr, dk1), d = (lr+1, dk1)
+    // Face planes of the cells of word w of own row lr (Sec. 3.3 face case):
+    // bit p of F[f] is set iff an intersected edge lies on face f of the cell at
+    // bit p.  Sample rows a = (lr, slice cz), b = (lr+1, cz), c = (lr, cz+1),
+    // d = (lr+1, cz+1); the previous word supplies the edge at bit 31 - 32.
+    auto faces = [&](int lr, int w, uint32_t (&F)[6]) {
         const uint32_t *aX = PL(0, 0, lr), *bX = PL(0, 0, lr + 1), *cX = PL(1, 0, lr), *dX = PL(1, 0, lr + 1);
         const uint32_t *aY = PL(0, 1, lr), *cY = PL(1, 1, lr), *aZ = PL(0, 2, lr), *bZ = PL(0, 2, lr + 1);
         const uint32_t Xa = aX[w], Xb = bX[w], Xc = cX[w], Xd = dX[w], Ya = aY[w], Yc = cY[w], Za = aZ[w], Zb = bZ[w];
@@ -174,21 +177,24 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
             pZa = aZ[w - 1];
             pZb = bZ[w - 1];
         }
-        uint32_t F[6];
         F[0] = shl1(Ya | Yc | Za | Zb, pYa | pYc | pZa | pZb);
         F[1] = Ya | Yc | Za | Zb;
         F[2] = shl1(Xa | Xc | Za, pXa | pXc | pZa) | Za;
         F[3] = shl1(Xb | Xd | Zb, pXb | pXd | pZb) | Zb;
         F[4] = shl1(Xa | Xb | Ya, pXa | pXb | pYa) | Ya;
         F[5] = shl1(Xc | Xd | Yc, pXc | pXd | pYc) | Yc;
+    };
+
+    // ---- stencil entries and quads of each word of the own rows, one thread per word
+    for (int it = tid; it < n * W; it += nthr) {
+        const int lr = (int)(((uint64_t)(uint32_t)it * tg.wdiv) >> 32), w = it - lr * W;
+        uint32_t F[6];
+        faces(lr, w, F);
         int deg = 0;
 #pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            sF[(lr * 6 + f) * W + w] = F[f];
-            deg += __popc(F[f]);
-        }
+        for (int f = 0; f < 6; ++f) deg += __popc(F[f]);
         sDpre[lr * W + w] = (uint16_t)deg;
-        sQpre[lr * W + w] = (uint16_t)(__popc(Xa) + __popc(Ya) + __popc(Za));
+        sQpre[lr * W + w] = (uint16_t)(__popc(PL(0, 0, lr)[w]) + __popc(PL(0, 1, lr)[w]) + __popc(PL(0, 2, lr)[w]));
     }
     __syncthreads();
     // ---- per-row exclusive prefixes, one thread per row: first point id of each
@@ -232,34 +238,33 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
             uint32_t bits = sP[sr * WS + w];
             int32_t t = sWB[sr * W + w] - pbase;
             if (!bits || t >= hi || t + __popc(bits) <= lo) continue;
+            uint32_t F[6];
+            faces(lr, w, F);
+            uint32_t wdeg = 0; // stencil entries of the word's points before this one
             while (bits) {
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1u;
-                if (t >= lo && t < hi) sList[t - lo] = ((uint32_t)lr << 11) | (uint32_t)(w * 32 + b);
+                uint32_t mask = 0;
+#pragma unroll
+                for (int f = 0; f < 6; ++f) mask |= ((F[f] >> b) & 1u) << f;
+                if (t >= lo && t < hi)
+                    sList[t - lo] = ((uint32_t)lr << 25) | ((uint32_t)(w * 32 + b) << 14) | (mask << 8) | wdeg;
+                wdeg += __popc(mask);
                 ++t;
             }
         }
         __syncthreads();
         for (int32_t k = lo + tid; k < hi; k += nthr) {
+            // entry: own row (5 bits) | cell bit (11) | face mask (6) | stencil entries before it in its word (8)
             const uint32_t e = sList[k - lo];
-            const int lr = (int)(e >> 11), p = (int)(e & 2047u), w = p >> 5, b = p & 31;
+            const int lr = (int)(e >> 25), p = (int)((e >> 14) & 2047u), w = p >> 5, b = p & 31;
+            const uint32_t mask = (e >> 8) & 63u;
             const int32_t id = pbase + k;
             if (id < 0 || id >= NP) continue;
             const uint32_t lt = (1u << b) - 1u;
             const int64_t cy = c0 - 1 + lr;
-            float *pt = m.points + 3 * (int64_t)id;
-            pt[0] = m.lut_x[p].x;
-            pt[1] = m.lut_y[cy + 1].x;
-            pt[2] = m.lut_z[czc].x;
             m.cells[id] = (uint64_t)p | ((uint64_t)(cy + 1) << 21) | ((uint64_t)czc << 42);
-            uint32_t mask = 0;
-            int64_t so = sSoff[lr] + sDpre[lr * W + w];
-#pragma unroll
-            for (int f = 0; f < 6; ++f) {
-                const uint32_t fw = sF[(lr * 6 + f) * W + w];
-                so += __popc(fw & lt);
-                mask |= ((fw >> b) & 1u) << f;
-            }
+            const int64_t so = sSoff[lr] + sDpre[lr * W + w] + (e & 255u);
             m.face_mask[id] = (uint8_t)mask;
             m.sten_off[id] = so;
             if (so < 0 || so + __popc(mask) > NS_) continue;
