@@ -63,6 +63,22 @@ cudaError_t emit_tile_m(int type, const void *labels, const Classifier &c, const
     return emit_tile_t<uint32_t, MODE>(labels, c, g, s, m, tot, tg, smem, st);
 }
 
+// Default cell rows per tile: the most (at most kEmitMaxRows, in steps of 4)
+// whose shared memory lets five tiles of kEmitThreads threads stay resident per
+// SM (228 KB per SM, 1 KB of it reserved per CTA).  Dense maps (many points per
+// row) gain from the residency; sparse ones from the longer tiles.
+int default_rows(int W, int WS)
+{
+#ifdef SN_EMIT_ROWS_FIXED
+    return kTileRows;
+#else
+    constexpr int kBudget = 228 * 1024 / 5 - 1024;
+    for (int r = kEmitMaxRows; r > 8; r -= 4)
+        if ((int)sizeof(uint32_t) * TileSmem(r, W, WS).total <= kBudget) return r;
+    return 8;
+#endif
+}
+
 } // namespace
 
 cudaError_t launch_emit_tile(int type, const void *labels, const Classifier &c, const Geometry &g,
@@ -71,7 +87,7 @@ cudaError_t launch_emit_tile(int type, const void *labels, const Classifier &c, 
     if (g.W > kTileMaxW || g.nz + 1 > 65535) return cudaErrorNotSupported;
     if (rows < 0 || rows > kEmitMaxRows) return cudaErrorInvalidValue;
     TileGeom tg;
-    tg.ty = rows ? rows : kTileRows;
+    tg.ty = rows ? rows : default_rows((int)g.W, (int)g.WS);
     tg.W = (int)g.W;
     tg.WS = (int)g.WS;
     tg.ns = 3 * (tg.ty + 2);

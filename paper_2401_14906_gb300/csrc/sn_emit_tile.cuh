@@ -11,7 +11,7 @@ namespace dev {
 #ifndef SN_EMIT_ROWS
 #define SN_EMIT_ROWS 24
 #endif
-constexpr int kTileRows = SN_EMIT_ROWS; // cell rows per tile of the single-map kernel
+constexpr int kTileRows = SN_EMIT_ROWS; // cell rows per tile when fixed (SN_EMIT_ROWS_FIXED)
 constexpr int kTileMaxW = 64;  // rows of up to 2047 cells; wider rows use the per-row kernel
 constexpr int kListCap = 2048; // entries of the tile's position list (one chunk of points or quads)
 
