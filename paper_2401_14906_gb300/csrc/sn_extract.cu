@@ -129,8 +129,17 @@ __global__ void __launch_bounds__(256) k_cellrows(Geometry g, ExtractScratch s)
     }
 }
 
+// threads per counting tile and the resident tiles per SM the registers are sized for
+#ifndef SN_COUNT_THREADS
+#define SN_COUNT_THREADS 256
+#endif
+#ifndef SN_COUNT_MINBLOCKS
+#define SN_COUNT_MINBLOCKS 4
+#endif
+constexpr int kCountThreads = SN_COUNT_THREADS;
+
 template <typename T, int MODE, bool FAST>
-__global__ void __launch_bounds__(256, 4) k_count(const T *__restrict__ lab, Classifier c, Geometry g, ExtractScratch s,
+__global__ void __launch_bounds__(kCountThreads, SN_COUNT_MINBLOCKS) k_count(const T *__restrict__ lab, Classifier c, Geometry g, ExtractScratch s,
                                                CountTiling tl, DevTotals *tot)
 {
     count_tile<T, MODE, FAST>(lab, c, g, s, tl, tot, blockIdx.x, tl.zt0 + (int64_t)blockIdx.y);
@@ -422,7 +431,7 @@ cudaError_t count_f(const void *labels, const Classifier &c, const Geometry &g, 
     if (e != cudaSuccess) return e;
     if (tl.zt1 <= tl.zt0) return cudaSuccess;
     dim3 grid((unsigned)((g.ny + tl.ty - 1) / tl.ty), (unsigned)(tl.zt1 - tl.zt0));
-    k_count<T, MODE, FAST><<<grid, 256, smem, st>>>((const T *)labels, c, g, s, tl, tot);
+    k_count<T, MODE, FAST><<<grid, kCountThreads, smem, st>>>((const T *)labels, c, g, s, tl, tot);
     return cudaGetLastError();
 }
 
@@ -541,7 +550,7 @@ bool count_tiling(int type, const void *labels, const Geometry &g, CountTiling *
     for (int t = 1; t <= kCountMaxTY; ++t) {
         if ((t + 1) * row_bytes > kSlotBudget) break;
         const int64_t items = (int64_t)(t + 1) * g.W;
-        const double fill = (double)(t * g.W) / (double)(((items + 255) / 256) * 256);
+        const double fill = (double)(t * g.W) / (double)(((items + kCountThreads - 1) / kCountThreads) * kCountThreads);
         if (fill > best + 1e-9) {
             best = fill;
             ty = t;
