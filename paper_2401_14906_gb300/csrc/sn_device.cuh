@@ -116,15 +116,12 @@ __device__ __forceinline__ NbrDist decode_record(uint2 v, uint32_t p, int rec, i
         d.dpz = p;
         return d;
     }
-    // 32-bit field extraction: the -y/+y fields lie in the low word (by <= 15,
-    // as bz >= by and 2 + 2 by + 2 bz <= 64); the -z field starts at or below
-    // bit 32 and the +z field, the topmost, may start on either side of it
-    const uint32_t my = (1u << by) - 1u, mz = (1u << bz) - 1u;
-    const int z0 = 2 + 2 * by, z1 = z0 + bz;
-    d.dmy = (v.x >> 2) & my;
-    d.dpy = (v.x >> (2 + by)) & my;
-    d.dmz = __funnelshift_rc(v.x, v.y, z0) & mz;
-    d.dpz = z1 >= 32 ? v.y >> (z1 - 32) : __funnelshift_rc(v.x, v.y, z1) & mz;
+    const uint64_t r = ((uint64_t)v.y << 32) | v.x;
+    const uint64_t my = (1ull << by) - 1ull, mz = (1ull << bz) - 1ull;
+    d.dmy = (uint32_t)((r >> 2) & my);
+    d.dpy = (uint32_t)((r >> (2 + by)) & my);
+    d.dmz = (uint32_t)((r >> (2 + 2 * by)) & mz);
+    d.dpz = (uint32_t)(r >> (2 + 2 * by + bz));
     return d;
 }
 

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_cellrows(Geometry g, ExtractScratch s)
 #define SN_COUNT_THREADS 256
 #endif
 #ifndef SN_COUNT_MINBLOCKS
-#define SN_COUNT_MINBLOCKS 4
+#define SN_COUNT_MINBLOCKS 2
 #endif
 constexpr int kCountThreads = SN_COUNT_THREADS;
 
