@@ -926,7 +926,7 @@ sn_status sn_mesh_cells(const sn_mesh *m, const uint64_t **cells)
 sn_status sn_mesh_record_bytes(const sn_mesh *m, int *bytes_per_point)
 {
     if (!m || !bytes_per_point) return fail(SN_EINVAL, "mesh or output is NULL");
-    *bytes_per_point = m->a.rec == sn::REC_PACKED ? 8 : m->a.rec == sn::REC_WIDE ? 12 : 0;
+    *bytes_per_point = m->a.rec == sn::REC_WIDE ? 12 : m->a.rec == sn::REC_CSR ? 0 : 8;
     return SN_OK;
 }
 

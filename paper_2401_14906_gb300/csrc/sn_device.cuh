@@ -92,6 +92,10 @@ __device__ __forceinline__ void store_record(const MeshArrays &m, int32_t id, ui
         m.nbrp[id] = d[3];
         return;
     }
+    if (m.rec == REC_SPLIT) {
+        m.nbr[id] = make_uint2(flags | (d[0] << 2) | (d[1] << 17), d[2] | (d[3] << 16));
+        return;
+    }
     const int by = m.by, bz = m.bz;
     const uint64_t r = (uint64_t)flags | ((uint64_t)d[0] << 2) | ((uint64_t)d[1] << (2 + by)) |
                        ((uint64_t)d[2] << (2 + 2 * by)) | ((uint64_t)d[3] << (2 + 2 * by + bz));
@@ -109,11 +113,11 @@ __device__ __forceinline__ NbrDist decode_record(uint2 v, uint32_t p, int rec, i
     NbrDist d;
     d.mx = v.x & 1u;
     d.px = (v.x >> 1) & 1u;
-    if (rec == REC_WIDE) {
+    if (rec == REC_WIDE || rec == REC_SPLIT) {
         d.dmy = (v.x >> 2) & 0x7fffu;
         d.dpy = v.x >> 17;
-        d.dmz = v.y;
-        d.dpz = p;
+        d.dmz = rec == REC_WIDE ? v.y : v.y & 0xffffu;
+        d.dpz = rec == REC_WIDE ? p : v.y >> 16;
         return d;
     }
     const uint64_t r = ((uint64_t)v.y << 32) | v.x;

@@ -650,6 +650,11 @@ int rec_mode(const DevTotals &t, int *by, int *bz)
 {
     *by = bits_for(t.yreach);
     *bz = bits_for(t.zreach);
+    if (*by <= 15 && *bz <= 16) {
+        *by = 15;
+        *bz = 16;
+        return REC_SPLIT;
+    }
     if (2 + 2 * *by + 2 * *bz <= 64) return REC_PACKED;
     *by = 15;
     *bz = 32;

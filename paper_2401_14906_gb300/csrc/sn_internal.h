@@ -79,7 +79,10 @@ struct DevTotals {
 //       order (by = 15), nbr.y = the 32-bit -z distance, nbrp = the +z distance
 //       (12 bytes per point); used when the -y/+y distances fit 15 bits.
 //   REC_CSR: the sweeps read the CSR stencil (rows of more than ~16k points).
-enum RecMode { REC_PACKED = 0, REC_WIDE = 1, REC_CSR = 2 };
+//   REC_SPLIT: REC_PACKED's fields at fixed places when they fit (by <= 15,
+//       bz <= 16): nbr.x as for REC_WIDE, nbr.y = d(-z) | d(+z) << 16; the
+//       cheapest to decode.
+enum RecMode { REC_PACKED = 0, REC_WIDE = 1, REC_CSR = 2, REC_SPLIT = 3 };
 
 // Output arrays of a mesh.
 struct MeshArrays {

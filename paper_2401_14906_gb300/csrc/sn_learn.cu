@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kLearnThreads) k_learn_features(MeshArrays m, 
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = k >> 1;
     if (i >= np) return;
-    const bool packed = m.rec == REC_PACKED;
+    const bool packed = m.rec == REC_PACKED || m.rec == REC_SPLIT;
     point_features(m, i, (int)(k & 1), hbits, packed, feature_loads(m, i, packed), X + i * kIn);
 }
 
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kLearnThreads) k_learn_propose(const uint16_t 
     load_weights(s, wq, params);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const bool packed = m.rec == REC_PACKED;
+    const bool packed = m.rec == REC_PACKED || m.rec == REC_SPLIT;
     const int64_t stride = (int64_t)gridDim.x * 4;
     int64_t tile = (int64_t)blockIdx.x * 4 + warp;
     FeatPre cur = {0u, make_uint2(0u, 0u), 0};

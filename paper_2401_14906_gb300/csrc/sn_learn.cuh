@@ -69,7 +69,7 @@ __device__ __forceinline__ void point_features(const MeshArrays &m, int64_t i, i
     }
     int64_t nb[3];
     if (packed) {
-        const dev::NbrDist d = dev::decode_record(p.r, 0u, REC_PACKED, m.by, m.bz);
+        const dev::NbrDist d = dev::decode_record(p.r, 0u, m.rec, m.by, m.bz);
         if (half == 0) {
             nb[0] = i - 1;
             nb[1] = i + 1;

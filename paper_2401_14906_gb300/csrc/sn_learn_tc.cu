@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kTcThreads) k_learn_propose_tc(const uint16_t 
     __syncthreads();
     fence_after();
     const uint32_t tmem = s.tmem;
-    const bool packed = m.rec == REC_PACKED;
+    const bool packed = m.rec == REC_PACKED || m.rec == REC_SPLIT;
     bool failed = false;
 
     if (warp >= 4) {

@@ -13,8 +13,10 @@
 // -x/+x neighbours are always id-1/id+1 (one presence bit each), and the
 // -y/+y/-z/+z neighbours are stored as id distances (0 = absent).  The record
 // is 8 bytes whenever the distances allowed by the mesh's reach bounds fit 62
-// bits together (REC_PACKED, field widths per mesh: 11 + 11 bits for -y/+y
-// and 20 + 20 for -z/+z on the 1024^2 x 512 connectome-like map); else 12 bytes
+// bits together: at fixed places (REC_SPLIT: 15-bit -y/+y and 16-bit -z/+z
+// fields, as on the 512^3 atlas-like map) or with field widths per mesh
+// (REC_PACKED: 11 + 11 bits for -y/+y and 20 + 20 for -z/+z on the 1024^2 x 512
+// connectome-like map); else 12 bytes
 // (REC_WIDE, 32-bit -z/+z distances).  Per point a sweep streams 12 B in + 12 B
 // out + the record from HBM; neighbours are gathered from L2 or L1.  Rows of
 // more than ~16k points, whose -y/+y distances may not fit 15 bits, use the CSR
@@ -49,7 +51,7 @@ struct SweepArgs {
     int first, last; // first sweep: offsets are all zero; last sweep: also write world coordinates
     int sphere;      // constrain |o| <= h instead of |o_a| <= h per axis
     int rec;         // RecMode of the mesh
-    int by, bz;      // REC_PACKED field widths
+    int by, bz;      // field widths (REC_PACKED)
 };
 
 // The constraint of Sec. 2.2: a box of half-width h per axis, or a ball of radius h.
