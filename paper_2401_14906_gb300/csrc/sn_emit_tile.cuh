@@ -229,25 +229,10 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
     const int last = slot_of(1, n - 1);
     const int32_t pbase = sWB[slot_of(1, 0) * W];
     const int32_t npts = sWB[last * W + (W - 1)] + __popc(sP[last * WS + (W - 1)]) - pbase;
-    // the words whose points start before position x of the tile: words are in
-    // id order, so a chunk's words are a run of them, found by binary search
-    auto pwords_before = [&](int32_t x) {
-        int a = 0, b = n * W; // count of words it with t(it) < x
-        while (a < b) {
-            const int mid = (a + b) >> 1;
-            const int lr = (int)(((uint64_t)(uint32_t)mid * tg.wdiv) >> 32);
-            if (sWB[slot_of(1, lr) * W + (mid - lr * W)] - pbase < x) a = mid + 1;
-            else b = mid;
-        }
-        return a;
-    };
     for (int32_t lo = 0; lo < npts; lo += kListCap) {
         const int32_t hi = npts - lo < kListCap ? npts : lo + kListCap;
-        // words [wa, wb): the word holding position lo (the last one starting at or before it) up to the last
-        // word starting before hi
-        const int wa0 = pwords_before(lo + 1), wa = wa0 > 0 ? wa0 - 1 : 0, wb = pwords_before(hi);
         __syncthreads(); // the previous chunk's list is read no more
-        for (int it = wa + tid; it < wb; it += nthr) {
+        for (int it = tid; it < n * W; it += nthr) {
             const int lr = (int)(((uint64_t)(uint32_t)it * tg.wdiv) >> 32), w = it - lr * W;
             const int sr = slot_of(1, lr);
             uint32_t bits = sP[sr * WS + w];
@@ -307,22 +292,10 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
     const int32_t nqt = (int32_t)(sQoff[n - 1] - qbase) + (int32_t)sQpre[(n - 1) * W + (W - 1)] +
                         __popc(PL(0, 0, n - 1)[W - 1]) + __popc(PL(0, 1, n - 1)[W - 1]) +
                         __popc(PL(0, 2, n - 1)[W - 1]);
-    auto qwords_before = [&](int32_t x) {
-        int a = lr_first * W, b = n * W; // lr_first * W + count of words it >= lr_first * W with t(it) < x
-        while (a < b) {
-            const int mid = (a + b) >> 1;
-            const int lr = (int)(((uint64_t)(uint32_t)mid * tg.wdiv) >> 32);
-            if ((int32_t)(sQoff[lr] - qbase) + (int32_t)sQpre[mid] < x) a = mid + 1;
-            else b = mid;
-        }
-        return a;
-    };
     for (int32_t lo = 0; lo < nqt; lo += kListCap) {
         const int32_t hi = nqt - lo < kListCap ? nqt : lo + kListCap;
-        const int wa0 = qwords_before(lo + 1), wa = wa0 > lr_first * W ? wa0 - 1 : lr_first * W,
-                  wb = qwords_before(hi);
         __syncthreads();
-        for (int it = wa + tid; it < wb; it += nthr) {
+        for (int it = lr_first * W + tid; it < n * W; it += nthr) {
             const int lr = (int)(((uint64_t)(uint32_t)it * tg.wdiv) >> 32), w = it - lr * W;
             const uint32_t qx = PL(0, 0, lr)[w], qy = PL(0, 1, lr)[w], qz = PL(0, 2, lr)[w];
             uint32_t bits = qx | qy | qz;
