@@ -1,7 +1,5 @@
 // sn_smooth.cu -- constrained Laplacian smoothing (Sec. 2.2 Eq. 1, Sec. 2.4) of one
 // mesh: one launch per Jacobi sweep (the sweep itself is in sn_sweep.cuh).
-#include <atomic>
-
 #include "sn_sweep.cuh"
 
 namespace sn {
@@ -10,13 +8,10 @@ namespace {
 
 using namespace dev;
 
-// One Jacobi sweep: CTA x takes blocks x, x + gridDim.x, ...
-#ifndef SN_SWEEP_MINBLOCKS
-#define SN_SWEEP_MINBLOCKS 1
-#endif
-__global__ void __launch_bounds__(kSweepThreads, SN_SWEEP_MINBLOCKS) k_smooth(SweepArgs a)
+// One Jacobi sweep over kSweepPoints points per CTA.
+__global__ void __launch_bounds__(kSweepThreads) k_smooth(SweepArgs a)
 {
-    sweep_blocks<false>(a, blockIdx.x, gridDim.x);
+    sweep_block<false>(a, blockIdx.x * (uint32_t)kSweepPoints);
 }
 
 __global__ void __launch_bounds__(256) k_centres(MeshArrays m, int64_t np)
@@ -73,9 +68,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_smooth_batch(const SmoothBatc
     a.first = t == 0;
     a.last = t == iterations - 1;
     a.sphere = sphere;
-    a.nblocks = (uint32_t)((mp.np + kSweepPoints - 1) / kSweepPoints);
-    sweep_blocks<false>(a, b - block_start[lo], a.nblocks); // one block per CTA
-
+    sweep_block<false>(a, (b - block_start[lo]) * (uint32_t)kSweepPoints);
 }
 
 // world positions from the offsets in `o`
@@ -92,34 +85,9 @@ __global__ void __launch_bounds__(256) k_world(MeshArrays m, const float *o, int
 }
 
 // Launches sweep `a` on st; `dependent`: as a programmatic dependent of the
-// kernel before it on the stream (the previous sweep), see sweep_blocks.
-// CTAs of a sweep launch: one per block, or (SN_SWEEP_PERSIST) at most the
-// resident CTAs of the GPU, which then stride over the blocks.
-#ifndef SN_SWEEP_PERSIST
-#define SN_SWEEP_PERSIST 1
-#endif
-unsigned sweep_grid(unsigned blocks)
-{
-    if (!SN_SWEEP_PERSIST) return blocks;
-    static std::atomic<int> resident{0};
-    int r = resident.load();
-    if (r == 0) {
-        int dev = 0, sms = 0, per = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_smooth, kSweepThreads, 0) != cudaSuccess) {
-            cudaGetLastError();
-            return blocks;
-        }
-        r = sms * (per > 0 ? per : 1);
-        resident.store(r);
-    }
-    return blocks < (unsigned)r ? blocks : (unsigned)r;
-}
-
+// kernel before it on the stream (the previous sweep), see sweep_block.
 cudaError_t launch_sweep(const SweepArgs &a, unsigned blocks, bool dependent, cudaStream_t st)
 {
-    blocks = sweep_grid(blocks);
     if (!dependent) {
         k_smooth<<<blocks, kSweepThreads, 0, st>>>(a);
         return cudaGetLastError();
@@ -181,7 +149,6 @@ cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float
     float *dst = (iterations % 2 == 1) ? m.offsets : scratch;
     cudaError_t e = cudaSuccess;
     const unsigned blocks = (unsigned)((np + kSweepPoints - 1) / kSweepPoints);
-    a.nblocks = blocks;
     for (int t = 0; t < iterations; ++t) {
         a.oin = src;
         a.oout = dst;
@@ -240,7 +207,6 @@ cudaError_t launch_smooth_from(const MeshArrays &m, int64_t np, int iterations, 
     float *src = start;
     float *dst = start == m.offsets ? scratch : m.offsets;
     const unsigned blocks = (unsigned)((np + kSweepPoints - 1) / kSweepPoints);
-    a.nblocks = blocks;
     for (int t = 0; t < iterations; ++t) {
         a.oin = src;
         a.oout = dst;

@@ -52,7 +52,6 @@ struct SweepArgs {
     int sphere;      // constrain |o| <= h instead of |o_a| <= h per axis
     int rec;         // RecMode of the mesh
     int by, bz;      // field widths (REC_PACKED)
-    uint32_t nblocks; // blocks of kSweepPoints points in the sweep
 };
 
 // The constraint of Sec. 2.2: a box of half-width h per axis, or a ball of radius h.
@@ -165,79 +164,53 @@ template <bool COH> __device__ __forceinline__ void sweep_point_csr(const SweepA
 constexpr int kSweepPPT = SN_SWEEP_PPT; // points per thread
 constexpr int kSweepThreads = SN_SWEEP_THREADS, kSweepPoints = kSweepPPT * kSweepThreads;
 
-// Blocks b0, b0 + stride, ... of one Jacobi sweep; block b holds points
-// [b * kSweepPoints, (b + 1) * kSweepPoints).  Each thread updates PPT points
-// kSweepThreads apart per block.  A grid of one CTA per block runs each CTA
-// once; a grid of the resident CTAs strides over the blocks, and each CTA
-// loads the neighbour records and own offsets of its next block before it
-// gathers the neighbours of the current one, so that the streamed loads of
-// the next block overlap the gathers of this one.  The first sweep starts from
-// zero offsets and reads none.  The record mode a.rec is the same in every
-// thread.
+// Points [base, base + PPT * kSweepThreads) of one Jacobi sweep.  Each thread
+// updates PPT points kSweepThreads apart; the own offsets and neighbour records
+// of all of them are loaded before any point's neighbours are gathered, so that
+// PPT times as many loads are in flight.  The first sweep starts from zero
+// offsets and reads none.  The record mode a.rec is the same in every thread.
 //
 // Sweeps after the first are launched as programmatic dependents of the sweep
 // before them: every block lets the next sweep's blocks be scheduled at once,
-// loads its first neighbour records (written by the extraction, never by a
-// sweep), and only then waits for the previous sweep to finish before it reads
-// or writes any offsets.  A launch without that attribute returns from the
-// wait at once.
+// loads its neighbour records (written by the extraction, never by a sweep),
+// and only then waits for the previous sweep to finish before it reads or
+// writes any offsets.  A launch without that attribute returns from the wait
+// at once.
 template <bool COH, int PPT = kSweepPPT>
-__device__ __forceinline__ void sweep_blocks(const SweepArgs &a, uint32_t b0, uint32_t stride)
+__device__ __forceinline__ void sweep_block(const SweepArgs &a, uint32_t base)
 {
     const uint64_t np = (uint64_t)a.np;
-    const uint32_t nblocks = a.nblocks;
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (a.rec == REC_CSR) {
         asm volatile("griddepcontrol.wait;" ::: "memory");
-        for (uint32_t b = b0; b < nblocks; b += stride)
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                const uint32_t i = b * (uint32_t)kSweepPoints + threadIdx.x + q * kSweepThreads;
-                if (i < np) sweep_point_csr<COH>(a, i);
-            }
+        for (int q = 0; q < PPT; ++q) {
+            const uint32_t i = base + threadIdx.x + q * kSweepThreads;
+            if (i < np) sweep_point_csr<COH>(a, i);
+        }
         return;
     }
-    const bool wide = a.rec == REC_WIDE;
-    auto load_records = [&](uint32_t b, NbrDist (&r)[PPT]) {
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-            const uint64_t i = (uint64_t)b * kSweepPoints + threadIdx.x + q * kSweepThreads;
-            const uint2 v = i < np ? a.nbr[i] : make_uint2(0u, 0u);
-            const uint32_t p = (wide && i < np) ? a.nbrp[i] : 0u;
-            r[q] = decode_record(v, p, a.rec, a.by, a.bz);
-        }
-    };
-    auto load_own = [&](uint32_t b, float3 (&o)[PPT]) {
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-            const uint64_t i = (uint64_t)b * kSweepPoints + threadIdx.x + q * kSweepThreads;
-            o[q] = make_float3(0.f, 0.f, 0.f);
-            if (i < np && !a.first) o[q] = ld3<COH>(a.oin, (uint32_t)i);
-        }
-    };
-    NbrDist r[PPT];
     float3 o[PPT];
-    uint32_t b = b0;
-    load_records(b, r);
+    NbrDist r[PPT];
+    const bool wide = a.rec == REC_WIDE;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const uint32_t i = base + threadIdx.x + q * kSweepThreads;
+        const uint2 v = i < np ? a.nbr[i] : make_uint2(0u, 0u);
+        const uint32_t p = (wide && i < np) ? a.nbrp[i] : 0u;
+        r[q] = decode_record(v, p, a.rec, a.by, a.bz);
+    }
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    load_own(b, o);
-    while (b < nblocks) {
-        const uint32_t nb = b + stride;
-        NbrDist rn[PPT];
-        float3 on[PPT];
-        load_records(nb, rn);
-        load_own(nb, on);
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-            const uint32_t i = b * (uint32_t)kSweepPoints + threadIdx.x + q * kSweepThreads;
-            if (i < np) sweep_point<COH>(a, i, o[q], r[q]);
-        }
+    for (int q = 0; q < PPT; ++q) {
+        const uint32_t i = base + threadIdx.x + q * kSweepThreads;
+        o[q] = make_float3(0.f, 0.f, 0.f);
+        if (i < np && !a.first) o[q] = ld3<COH>(a.oin, i);
+    }
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-            r[q] = rn[q];
-            o[q] = on[q];
-        }
-        b = nb;
+    for (int q = 0; q < PPT; ++q) {
+        const uint32_t i = base + threadIdx.x + q * kSweepThreads;
+        if (i < np) sweep_point<COH>(a, i, o[q], r[q]);
     }
 }
 
