@@ -1671,6 +1671,9 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
     sn::SmoothBatchMap *smooth_table = nullptr;
     uint32_t *smooth_table_blocks = nullptr;
     uint32_t total_blocks = 0;
+    bool fusable = true; // sweeps 1 and 2 in one launch: every mesh has neighbour records
+    for (int64_t i = 0; i < n_maps; ++i) fusable = fusable && jobs[i].mesh->a.rec != sn::REC_CSR;
+    const int launches = sn::sweep_launches(iterations, fusable);
     if (iterations > 0) {
         std::vector<sn::SmoothBatchMap> tab((size_t)n_maps);
         std::vector<uint32_t> starts((size_t)n_maps);
@@ -1682,9 +1685,9 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
             std::memset(&t, 0, sizeof(t));
             t.m = m->a;
             t.np = m->np;
-            // the first source is chosen so that the last sweep writes m.offsets
-            t.buf[0] = (iterations % 2 == 1) ? m->smooth_scratch : m->a.offsets;
-            t.buf[1] = (iterations % 2 == 1) ? m->a.offsets : m->smooth_scratch;
+            // the first source is chosen so that the last launch writes m.offsets
+            t.buf[0] = (launches % 2 == 1) ? m->smooth_scratch : m->a.offsets;
+            t.buf[1] = (launches % 2 == 1) ? m->a.offsets : m->smooth_scratch;
             t.spx = (float)m->spacing[0];
             t.spy = (float)m->spacing[1];
             t.spz = (float)m->spacing[2];
@@ -1739,7 +1742,7 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
     // the sweeps of all meshes: one launch per sweep
     if (iterations > 0 && smooth_table) {
         e = sn::launch_smooth_batch(smooth_table, smooth_table_blocks, (int)n_maps, total_blocks, iterations,
-                                    relaxation, half, 0, origin_st);
+                                    fusable, relaxation, half, 0, origin_st);
         if (e != cudaSuccess) return finish(cuda_fail(e, "smoothing launch"));
     }
     if (use_graph) {

@@ -216,9 +216,12 @@ struct SmoothBatchMap {
     int pad;
 };
 int smooth_points_per_block();
+// Launches that run `iterations` sweeps from zero offsets: sweeps 1 and 2 share
+// one launch when `fusable` (the meshes have neighbour records, not the CSR).
+int sweep_launches(int iterations, bool fusable);
 cudaError_t launch_smooth_batch(const SmoothBatchMap *maps, const uint32_t *block_start, int n_maps,
-                                uint32_t total_blocks, int iterations, float relaxation, float half, int sphere,
-                                cudaStream_t st);
+                                uint32_t total_blocks, int iterations, bool fusable, float relaxation, float half,
+                                int sphere, cudaStream_t st);
 
 // learned smoothing proposal (sn_learn.cu); parameters in the layout of sn.h
 constexpr int kLearnParams = 6467;

@@ -8,10 +8,10 @@ namespace {
 
 using namespace dev;
 
-// One Jacobi sweep over kSweepPoints points per CTA.
-__global__ void __launch_bounds__(kSweepThreads) k_smooth(SweepArgs a)
+// One Jacobi sweep over kSweepPoints points per CTA (FUSED: sweeps 1 and 2).
+template <bool FUSED> __global__ void __launch_bounds__(kSweepThreads) k_smooth(SweepArgs a)
 {
-    sweep_block<false>(a, blockIdx.x * (uint32_t)kSweepPoints);
+    sweep_block<false, FUSED>(a, blockIdx.x * (uint32_t)kSweepPoints);
 }
 
 __global__ void __launch_bounds__(256) k_centres(MeshArrays m, int64_t np)
@@ -28,11 +28,13 @@ __global__ void __launch_bounds__(256) k_centres(MeshArrays m, int64_t np)
     m.points[3 * i + 2] = m.lut_z[(c >> 42) & m21].x;
 }
 
-// One sweep t of many meshes: CTA b works on block b - block_start[i] of the
-// mesh i with block_start[i] <= b < block_start[i+1].
+// Launch t of the sweeps of many meshes: CTA b works on block b - block_start[i]
+// of the mesh i with block_start[i] <= b < block_start[i+1].  `fused`: launch 0
+// runs sweeps 1 and 2.
+template <bool FUSED>
 __global__ void __launch_bounds__(kSweepThreads) k_smooth_batch(const SmoothBatchMap *maps,
                                                                 const uint32_t *block_start, int n, int t,
-                                                                int iterations, float lam, float h, int sphere)
+                                                                int launches, float lam, float h, int sphere)
 {
     const uint32_t b = blockIdx.x;
     int lo = 0;
@@ -66,9 +68,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_smooth_batch(const SmoothBatc
     a.spy = mp.spy;
     a.spz = mp.spz;
     a.first = t == 0;
-    a.last = t == iterations - 1;
+    a.last = t == launches - 1;
     a.sphere = sphere;
-    sweep_block<false>(a, (b - block_start[lo]) * (uint32_t)kSweepPoints);
+    sweep_block<false, FUSED>(a, (b - block_start[lo]) * (uint32_t)kSweepPoints);
 }
 
 // world positions from the offsets in `o`
@@ -89,7 +91,8 @@ __global__ void __launch_bounds__(256) k_world(MeshArrays m, const float *o, int
 cudaError_t launch_sweep(const SweepArgs &a, unsigned blocks, bool dependent, cudaStream_t st)
 {
     if (!dependent) {
-        k_smooth<<<blocks, kSweepThreads, 0, st>>>(a);
+        if (a.first == 2) k_smooth<true><<<blocks, kSweepThreads, 0, st>>>(a);
+        else k_smooth<false><<<blocks, kSweepThreads, 0, st>>>(a);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -102,7 +105,7 @@ cudaError_t launch_sweep(const SweepArgs &a, unsigned blocks, bool dependent, cu
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_smooth, a);
+    return a.first == 2 ? cudaLaunchKernelEx(&cfg, k_smooth<true>, a) : cudaLaunchKernelEx(&cfg, k_smooth<false>, a);
 }
 
 } // namespace
@@ -144,16 +147,20 @@ cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float
     a.spx = (float)spacing[0];
     a.spy = (float)spacing[1];
     a.spz = (float)spacing[2];
-    // pick the first source so that the last sweep writes m.offsets (the first sweep reads no offsets)
-    float *src = (iterations % 2 == 1) ? scratch : m.offsets;
-    float *dst = (iterations % 2 == 1) ? m.offsets : scratch;
+    // sweeps 1 and 2 run as one launch (unless the sweeps read the CSR stencil);
+    // the first destination is chosen so that the last launch writes m.offsets
+    // (the first launch reads no offsets)
+    const bool fused = iterations >= 2 && m.rec != REC_CSR;
+    const int launches = sweep_launches(iterations, m.rec != REC_CSR);
+    float *dst = (launches % 2 == 1) ? m.offsets : scratch;
+    float *src = (launches % 2 == 1) ? scratch : m.offsets;
     cudaError_t e = cudaSuccess;
     const unsigned blocks = (unsigned)((np + kSweepPoints - 1) / kSweepPoints);
-    for (int t = 0; t < iterations; ++t) {
+    for (int t = 0; t < launches; ++t) {
         a.oin = src;
         a.oout = dst;
-        a.first = t == 0;
-        a.last = t == iterations - 1;
+        a.first = t == 0 ? (fused ? 2 : 1) : 0;
+        a.last = t == launches - 1;
         ProfScope ps("k_smooth", st);
         if ((e = launch_sweep(a, blocks, t > 0, st)) != cudaSuccess) return e;
         float *tmp = src;
@@ -227,15 +234,22 @@ namespace sn {
 
 int smooth_points_per_block() { return kSweepPoints; }
 
+int sweep_launches(int iterations, bool fusable) { return (fusable && iterations >= 2) ? iterations - 1 : iterations; }
+
 cudaError_t launch_smooth_batch(const SmoothBatchMap *maps, const uint32_t *block_start, int n_maps,
-                                uint32_t total_blocks, int iterations, float relaxation, float half, int sphere,
-                                cudaStream_t st)
+                                uint32_t total_blocks, int iterations, bool fusable, float relaxation, float half,
+                                int sphere, cudaStream_t st)
 {
     if (n_maps == 0 || total_blocks == 0) return cudaSuccess;
-    for (int t = 0; t < iterations; ++t) {
+    const int launches = sweep_launches(iterations, fusable);
+    for (int t = 0; t < launches; ++t) {
         ProfScope ps("k_smooth_batch", st);
-        k_smooth_batch<<<total_blocks, kSweepThreads, 0, st>>>(maps, block_start, n_maps, t, iterations, relaxation,
-                                                               half, sphere);
+        if (t == 0 && fusable && iterations >= 2)
+            k_smooth_batch<true><<<total_blocks, kSweepThreads, 0, st>>>(maps, block_start, n_maps, t, launches,
+                                                                         relaxation, half, sphere);
+        else
+            k_smooth_batch<false><<<total_blocks, kSweepThreads, 0, st>>>(maps, block_start, n_maps, t, launches,
+                                                                          relaxation, half, sphere);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

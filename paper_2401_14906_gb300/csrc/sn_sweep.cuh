@@ -48,7 +48,8 @@ struct SweepArgs {
     int64_t np;
     float lam, h;
     float spx, spy, spz;
-    int first, last; // first sweep: offsets are all zero; last sweep: also write world coordinates
+    int first;       // sweep 1 (all offsets are zero before it), or sweeps 1 and 2 at once (FUSED)
+    int last;        // the last sweep: also write world coordinates
     int sphere;      // constrain |o| <= h instead of |o_a| <= h per axis
     int rec;         // RecMode of the mesh
     int by, bz;      // field widths (REC_PACKED)
@@ -82,24 +83,57 @@ template <bool COH> __device__ __forceinline__ float3 ld3(const float *__restric
     return make_float3(q[0], q[1], q[2]);
 }
 
-// Neighbour sum and update of one point (neighbour record).
-template <bool COH> __device__ __forceinline__ void sweep_point(const SweepArgs &a, uint32_t i, float3 o, NbrDist r)
+// Stencil size and unit-step sum of a point from its decoded record.
+__device__ __forceinline__ int stencil_n(const NbrDist &r)
+{
+    return (int)(r.mx + r.px + (r.dmy != 0) + (r.dpy != 0) + (r.dmz != 0) + (r.dpz != 0));
+}
+__device__ __forceinline__ float3 unit_steps(const NbrDist &r)
+{
+    return make_float3((float)((int)r.px - (int)r.mx), (float)((int)(r.dpy != 0) - (int)(r.dmy != 0)),
+                       (float)((int)(r.dpz != 0) - (int)(r.dmz != 0)));
+}
+
+// The offset after sweep 1 of a point with record r.  All offsets are zero
+// before it, so Eq. 1 leaves lam / n times the sum of the unit steps towards
+// the neighbours, clamped: a function of the record alone, computed with the
+// same operations as the sweep (0 + lam/n * s).
+__device__ __forceinline__ float3 first_offset(const SweepArgs &a, const NbrDist &r)
+{
+    const float ln = a.lam * kInv[stencil_n(r)];
+    const float3 s = unit_steps(r);
+    return constrain(make_float3(0.f + ln * s.x, 0.f + ln * s.y, 0.f + ln * s.z), a.h, a.sphere);
+}
+
+// record of point j (REC_PACKED / REC_SPLIT / REC_WIDE)
+__device__ __forceinline__ NbrDist record_of(const SweepArgs &a, uint32_t j)
+{
+    return decode_record(a.nbr[j], a.rec == REC_WIDE ? a.nbrp[j] : 0u, a.rec, a.by, a.bz);
+}
+
+// Neighbour sum and update of one point (neighbour record).  FUSED: sweep 2
+// computed directly from the records, the point's own offset and its
+// neighbours' offsets after sweep 1 coming from first_offset (a separate
+// instantiation, so that the other sweeps keep their register budget).
+template <bool COH, bool FUSED> __device__ __forceinline__ void sweep_point(const SweepArgs &a, uint32_t i, float3 o,
+                                                                         NbrDist r)
 {
     const float *__restrict__ oin = a.oin;
     const uint32_t mx = r.mx, px = r.px, dmy = r.dmy, dpy = r.dpy, dmz = r.dmz, dpz = r.dpz;
-    const int n = (int)(mx + px + (dmy != 0) + (dpy != 0) + (dmz != 0) + (dpz != 0));
-    float3 acc = make_float3((float)((int)px - (int)mx), (float)((int)(dpy != 0) - (int)(dmy != 0)),
-                             (float)((int)(dpz != 0) - (int)(dmz != 0)));
+    const int n = stencil_n(r);
+    float3 acc = unit_steps(r);
+    if (FUSED) o = first_offset(a, r);
     // neighbours in face order -x, +x, -y, +y, -z, +z (all offsets are zero before the first sweep)
-    if (!a.first) {
+    if (FUSED || !a.first) {
         float3 sq = make_float3(0.f, 0.f, 0.f);
         auto add = [&](float3 q) { sq.x += q.x; sq.y += q.y; sq.z += q.z; };
-        if (mx) add(ld3<COH>(oin, i - 1));
-        if (px) add(ld3<COH>(oin, i + 1));
-        if (dmy) add(ld3<COH>(oin, i - dmy));
-        if (dpy) add(ld3<COH>(oin, i + dpy));
-        if (dmz) add(ld3<COH>(oin, i - dmz));
-        if (dpz) add(ld3<COH>(oin, i + dpz));
+        auto nb = [&](uint32_t j) { return FUSED ? first_offset(a, record_of(a, j)) : ld3<COH>(oin, j); };
+        if (mx) add(nb(i - 1));
+        if (px) add(nb(i + 1));
+        if (dmy) add(nb(i - dmy));
+        if (dpy) add(nb(i + dpy));
+        if (dmz) add(nb(i - dmz));
+        if (dpz) add(nb(i + dpz));
         const float fn = (float)n;
         acc.x += sq.x - fn * o.x;
         acc.y += sq.y - fn * o.y;
@@ -176,7 +210,7 @@ constexpr int kSweepThreads = SN_SWEEP_THREADS, kSweepPoints = kSweepPPT * kSwee
 // and only then waits for the previous sweep to finish before it reads or
 // writes any offsets.  A launch without that attribute returns from the wait
 // at once.
-template <bool COH, int PPT = kSweepPPT>
+template <bool COH, bool FUSED = false, int PPT = kSweepPPT>
 __device__ __forceinline__ void sweep_block(const SweepArgs &a, uint32_t base)
 {
     const uint64_t np = (uint64_t)a.np;
@@ -210,7 +244,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, uint32_t base)
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         const uint32_t i = base + threadIdx.x + q * kSweepThreads;
-        if (i < np) sweep_point<COH>(a, i, o[q], r[q]);
+        if (i < np) sweep_point<COH, FUSED>(a, i, o[q], r[q]);
     }
 }
 

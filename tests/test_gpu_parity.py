@@ -182,6 +182,17 @@ def test_zero_iterations_and_zero_relaxation():
     parity(lab, iterations=6, relaxation=1.0, constraint=0.0)
 
 
+@pytest.mark.parametrize("iterations", [1, 2, 3])
+@pytest.mark.parametrize("sphere", [False, True])
+def test_first_sweeps(iterations, sphere):
+    """Sweeps 1 and 2 run as one launch whose offsets after sweep 1 come from the neighbour records; one,
+    two and three sweeps, box and ball, 8- and 12-byte records."""
+    lab = sn_synth.ellipsoids((52, 47, 40), 5, 4.0, 15.0, np.uint16, seed=31)
+    parity(lab, spacing=(1.0, 0.9, 1.3), iterations=iterations, relaxation=0.7, constraint=0.8, sphere=sphere)
+    z, y, x = np.mgrid[0:3, 0:200, 0:2000]
+    parity(((x + y + z) % 2).astype(np.uint16), iterations=iterations, sphere=sphere, record_bytes=12)
+
+
 def test_sphere_constraint():
     lab = sn_synth.ellipsoids((60, 52, 44), 6, 5.0, 16.0, np.uint16, seed=12)
     parity(lab, iterations=16, sphere=True)
