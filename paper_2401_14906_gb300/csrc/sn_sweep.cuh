@@ -105,29 +105,36 @@ __device__ __forceinline__ float3 first_offset(const SweepArgs &a, const NbrDist
     return constrain(make_float3(0.f + ln * s.x, 0.f + ln * s.y, 0.f + ln * s.z), a.h, a.sphere);
 }
 
-// record of point j (REC_PACKED / REC_SPLIT / REC_WIDE)
-__device__ __forceinline__ NbrDist record_of(const SweepArgs &a, uint32_t j)
+// face mask (-x,+x,-y,+y,-z,+z) of a decoded record
+__device__ __forceinline__ uint32_t mask_of(const NbrDist &r)
 {
-    return decode_record(a.nbr[j], a.rec == REC_WIDE ? a.nbrp[j] : 0u, a.rec, a.by, a.bz);
+    return r.mx | (r.px << 1) | ((uint32_t)(r.dmy != 0) << 2) | ((uint32_t)(r.dpy != 0) << 3) |
+           ((uint32_t)(r.dmz != 0) << 4) | ((uint32_t)(r.dpz != 0) << 5);
 }
 
 // Neighbour sum and update of one point (neighbour record).  FUSED: sweep 2
-// computed directly from the records, the point's own offset and its
-// neighbours' offsets after sweep 1 coming from first_offset (a separate
-// instantiation, so that the other sweeps keep their register budget).
-template <bool COH, bool FUSED> __device__ __forceinline__ void sweep_point(const SweepArgs &a, uint32_t i, float3 o,
-                                                                         NbrDist r)
+// computed directly, the point's own offset and its neighbours' offsets after
+// sweep 1 taken from `first1`, the sweep-1 offset of each of the 64 face masks
+// (first_offset of that mask), indexed by the face masks of the extraction (a
+// separate instantiation, so that the other sweeps keep their register budget).
+template <bool COH, bool FUSED>
+__device__ __forceinline__ void sweep_point(const SweepArgs &a, uint32_t i, float3 o, NbrDist r,
+                                            const float4 *first1 = nullptr)
 {
     const float *__restrict__ oin = a.oin;
     const uint32_t mx = r.mx, px = r.px, dmy = r.dmy, dpy = r.dpy, dmz = r.dmz, dpz = r.dpz;
     const int n = stencil_n(r);
     float3 acc = unit_steps(r);
-    if (FUSED) o = first_offset(a, r);
+    auto f1 = [&](uint32_t mask) {
+        const float4 v = first1[mask];
+        return make_float3(v.x, v.y, v.z);
+    };
+    if (FUSED) o = f1(mask_of(r));
     // neighbours in face order -x, +x, -y, +y, -z, +z (all offsets are zero before the first sweep)
     if (FUSED || !a.first) {
         float3 sq = make_float3(0.f, 0.f, 0.f);
         auto add = [&](float3 q) { sq.x += q.x; sq.y += q.y; sq.z += q.z; };
-        auto nb = [&](uint32_t j) { return FUSED ? first_offset(a, record_of(a, j)) : ld3<COH>(oin, j); };
+        auto nb = [&](uint32_t j) { return FUSED ? f1(a.fmask[j]) : ld3<COH>(oin, j); };
         if (mx) add(nb(i - 1));
         if (px) add(nb(i + 1));
         if (dmy) add(nb(i - dmy));
@@ -227,6 +234,22 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, uint32_t base)
     float3 o[PPT];
     NbrDist r[PPT];
     const bool wide = a.rec == REC_WIDE;
+    __shared__ float4 first1[FUSED ? 64 : 1];
+    if (FUSED) {
+        if (threadIdx.x < 64) {
+            const uint32_t m = threadIdx.x;
+            NbrDist d;
+            d.mx = m & 1u;
+            d.px = (m >> 1) & 1u;
+            d.dmy = (m >> 2) & 1u;
+            d.dpy = (m >> 3) & 1u;
+            d.dmz = (m >> 4) & 1u;
+            d.dpz = (m >> 5) & 1u;
+            const float3 v = first_offset(a, d);
+            first1[m] = make_float4(v.x, v.y, v.z, 0.f);
+        }
+        __syncthreads();
+    }
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         const uint32_t i = base + threadIdx.x + q * kSweepThreads;
@@ -244,7 +267,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, uint32_t base)
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         const uint32_t i = base + threadIdx.x + q * kSweepThreads;
-        if (i < np) sweep_point<COH, FUSED>(a, i, o[q], r[q]);
+        if (i < np) sweep_point<COH, FUSED>(a, i, o[q], r[q], first1);
     }
 }
 
