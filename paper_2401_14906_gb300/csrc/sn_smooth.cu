@@ -9,7 +9,7 @@ namespace {
 using namespace dev;
 
 // One Jacobi sweep over kSweepPoints points per CTA (FUSED: sweeps 1 and 2).
-template <bool FUSED> __global__ void __launch_bounds__(kSweepThreads) k_smooth(SweepArgs a)
+template <bool FUSED> __global__ void __launch_bounds__(kSweepThreads, 2048 / kSweepThreads) k_smooth(SweepArgs a)
 {
     sweep_block<false, FUSED>(a, blockIdx.x * (uint32_t)kSweepPoints);
 }
@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256) k_centres(MeshArrays m, int64_t np)
 // of the mesh i with block_start[i] <= b < block_start[i+1].  `fused`: launch 0
 // runs sweeps 1 and 2.
 template <bool FUSED>
-__global__ void __launch_bounds__(kSweepThreads) k_smooth_batch(const SmoothBatchMap *maps,
+__global__ void __launch_bounds__(kSweepThreads, 2048 / kSweepThreads) k_smooth_batch(const SmoothBatchMap *maps,
                                                                 const uint32_t *block_start, int n, int t,
                                                                 int launches, float lam, float h, int sphere)
 {
