@@ -176,6 +176,8 @@ def kernel_units(name, V, b, P, Q, S, n):
     """(algorithmic bytes per launch, unit description) for each kernel."""
     if name == "k_smooth":
         return 24 * P, "24 B per point (read+write one float3 offset)"
+    if name == "k_smooth_first2":
+        return 48 * P, "48 B per point (sweeps 1 and 2: read+write one float3 offset each)"
     if name in ("k_count", "k_planes"):
         return V * b, "%d B per voxel (labels read once)" % b
     if name in ("k_emit_tile", "k_emit"):

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256) k_centres(MeshArrays m, int64_t np)
 // of the mesh i with block_start[i] <= b < block_start[i+1].  `fused`: launch 0
 // runs sweeps 1 and 2.
 template <bool FUSED>
-__global__ void __launch_bounds__(kSweepThreads, 2048 / kSweepThreads) k_smooth_batch(const SmoothBatchMap *maps,
+__global__ void __launch_bounds__(kSweepThreads) k_smooth_batch(const SmoothBatchMap *maps,
                                                                 const uint32_t *block_start, int n, int t,
                                                                 int launches, float lam, float h, int sphere)
 {
@@ -161,7 +161,7 @@ cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float
         a.oout = dst;
         a.first = t == 0 ? (fused ? 2 : 1) : 0;
         a.last = t == launches - 1;
-        ProfScope ps("k_smooth", st);
+        ProfScope ps(a.first == 2 ? "k_smooth_first2" : "k_smooth", st);
         if ((e = launch_sweep(a, blocks, t > 0, st)) != cudaSuccess) return e;
         float *tmp = src;
         src = dst;
