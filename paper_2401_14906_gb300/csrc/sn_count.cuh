@@ -18,7 +18,11 @@ namespace dev {
 // cz and cz+1 (kept in shared memory) into the face and point planes of cell
 // rows (cy, cz) with their point and stencil counts (Pass 3).  Every label is
 // read from HBM once; halo rows and the halo slice come from L2.
-constexpr int kCountSlots = 3;
+#ifndef SN_COUNT_SLOTS
+#define SN_COUNT_SLOTS 3
+#endif
+constexpr int kCountSlots = SN_COUNT_SLOTS; // label slices in flight per tile (a ring of TMA destinations)
+static_assert(kCountSlots >= 3 && kCountSlots <= 4, "the header holds four mbarriers before the row counters");
 constexpr int kCountMaxTY = 16;    // rows per tile, at most
 constexpr int kCountHeader = 1024; // mbarriers (24 B) + two sets of row counters (2 * (3*16+2) ints) fit in 1024 bytes
 static_assert(32 + 2 * (3 * kCountMaxTY + 2) * 4 <= kCountHeader, "row counters overflow the header");

@@ -542,7 +542,10 @@ cudaError_t launch_epilogue_batch(const BatchMeshPrep *maps, int n, cudaStream_t
 bool count_tiling(int type, const void *labels, const Geometry &g, CountTiling *out, size_t *smem_out)
 {
     const int64_t row_bytes = g.lp * (int64_t)type; // label rows are g.lp elements apart
-    constexpr int64_t kSlotBudget = 24 * 1024; // bytes of labels per slot
+#ifndef SN_COUNT_SLOT_KB
+#define SN_COUNT_SLOT_KB 24
+#endif
+    constexpr int64_t kSlotBudget = SN_COUNT_SLOT_KB * 1024; // bytes of labels per slot
     // rows per tile: fit the slot budget, and make the (rows + 1) * W edge-word
     // items of a slice fill the 256 threads as evenly as possible
     int ty = 0;
