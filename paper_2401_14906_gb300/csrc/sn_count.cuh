@@ -24,7 +24,7 @@ namespace dev {
 constexpr int kCountSlots = SN_COUNT_SLOTS; // label slices in flight per tile (a ring of TMA destinations)
 static_assert(kCountSlots >= 3 && kCountSlots <= 4, "the header holds four mbarriers before the row counters");
 #ifndef SN_COUNT_MAX_TY
-#define SN_COUNT_MAX_TY 16
+#define SN_COUNT_MAX_TY 32
 #endif
 constexpr int kCountMaxTY = SN_COUNT_MAX_TY; // rows per tile, at most
 constexpr int kCountHeader = 1024; // mbarriers (24 B) + two sets of row counters (2 * (3*16+2) ints) fit in 1024 bytes

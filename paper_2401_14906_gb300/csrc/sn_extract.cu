@@ -543,7 +543,7 @@ bool count_tiling(int type, const void *labels, const Geometry &g, CountTiling *
 {
     const int64_t row_bytes = g.lp * (int64_t)type; // label rows are g.lp elements apart
 #ifndef SN_COUNT_SLOT_KB
-#define SN_COUNT_SLOT_KB 24
+#define SN_COUNT_SLOT_KB 32
 #endif
     constexpr int64_t kSlotBudget = SN_COUNT_SLOT_KB * 1024; // bytes of labels per slot
     // rows per tile: fit the slot budget, and make the (rows + 1) * W edge-word

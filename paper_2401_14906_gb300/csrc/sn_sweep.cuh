@@ -76,10 +76,14 @@ __device__ __forceinline__ void add_diff(float3 &acc, float3 q, float3 o)
 }
 
 // COH: read through L2 only (offsets written by other CTAs of the same launch)
+#ifndef SN_SWEEP_LDG
+#define SN_SWEEP_LDG 0
+#endif
 template <bool COH> __device__ __forceinline__ float3 ld3(const float *__restrict__ p, uint32_t j)
 {
     const float *q = p + 3ull * j;
     if (COH) return make_float3(__ldcg(q), __ldcg(q + 1), __ldcg(q + 2));
+    if (SN_SWEEP_LDG) return make_float3(__ldg(q), __ldg(q + 1), __ldg(q + 2));
     return make_float3(q[0], q[1], q[2]);
 }
 
