@@ -347,7 +347,10 @@ sn_status sn_mesh_face_masks(const sn_mesh *m, const uint8_t **face_masks);
 
 /* Borrowed device pointer to each point's generating cell, packed as uint64
  * (cx+1) | (cy+1) << 21 | (cz+1) << 42 with c in [-1, n-1] per axis (the
- * dual cells of Sec. 2.2); point ids are ordered by (cz, cy, cx). */
+ * dual cells of Sec. 2.2); point ids are ordered by (cz, cy, cx).  Meshes whose
+ * extents fit keep 32-bit codes internally; for them the first call allocates
+ * this array (owned by the mesh) and fills it on the mesh's stream.  Errors:
+ * SN_EINVAL, SN_ENOMEM, SN_ECUDA. */
 sn_status sn_mesh_cells(const sn_mesh *m, const uint64_t **cells);
 
 /* Bytes per point of the neighbour record the smoothing sweeps stream (Sec. 2.4

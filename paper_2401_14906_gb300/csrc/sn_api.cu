@@ -33,6 +33,7 @@ struct sn_mesh {
     cudaEvent_t extracted; // recorded once the extraction outputs are final (their copies can overlap the smoothing)
     cudaEvent_t copied;    // the last sn_mesh_copy_to_host_async has finished
     int32_t *copy_meta;    // its copy of the meta words (pinned)
+    uint64_t *cells64;     // the cell codes as sn_mesh_cells hands them out, made on first request (32-bit codes)
     bool copy_pending;
     // The extraction writes neither the world positions nor the offsets (a
     // smoothing writes them all); until something does, they are set to the cell
@@ -561,6 +562,18 @@ sn_status job_allocate(ExtractJob &j, cudaStream_t st, bool with_smooth_buffer =
     m->ns = ns;
     m->a.rec = sn::rec_mode(*htot, &m->a.by, &m->a.bz);
     const int64_t nx = j.dims[0], ny = j.dims[1], nz = j.dims[2];
+    {
+        // cell codes in 32 bits when the three extents (cell coordinate + 1 in [0, n]) fit
+        auto bits = [](int64_t v) {
+            int b = 1;
+            while ((1ll << b) <= v) ++b;
+            return b;
+        };
+        const int bx = bits(nx), byy = bits(ny), bzz = bits(nz);
+        m->a.cell_wide = bx + byy + bzz > 32;
+        m->a.cell_sy = m->a.cell_wide ? 21 : bx;
+        m->a.cell_sz = m->a.cell_wide ? 42 : bx + byy;
+    }
     struct {
         void **p;
         size_t bytes;
@@ -568,7 +581,7 @@ sn_status job_allocate(ExtractJob &j, cudaStream_t st, bool with_smooth_buffer =
     } oplan[] = {
         {(void **)&m->a.points, sizeof(float) * 3 * (size_t)np, "points"},
         {(void **)&m->a.offsets, sizeof(float) * 3 * (size_t)np, "offsets"},
-        {(void **)&m->a.cells, sizeof(uint64_t) * (size_t)np, "cells"},
+        {(void **)&m->a.cells, (m->a.cell_wide ? sizeof(uint64_t) : sizeof(uint32_t)) * (size_t)np, "cells"},
         {(void **)&m->a.quads, sizeof(int32_t) * 4 * (size_t)nq, "quads"},
         {(void **)&m->a.quad_labels, (size_t)j.type * 2 * (size_t)nq, "quad labels"},
         {(void **)&m->a.sten_off, sizeof(int64_t) * (size_t)(np + 1), "stencil offsets"},
@@ -916,10 +929,26 @@ sn_status sn_mesh_face_masks(const sn_mesh *m, const uint8_t **face_masks)
     return SN_OK;
 }
 
-sn_status sn_mesh_cells(const sn_mesh *m, const uint64_t **cells)
+sn_status sn_mesh_cells(const sn_mesh *cm, const uint64_t **cells)
 {
-    if (!m || !cells) return fail(SN_EINVAL, "mesh or output is NULL");
-    *cells = m->a.cells;
+    if (!cm || !cells) return fail(SN_EINVAL, "mesh or output is NULL");
+    sn_mesh *m = const_cast<sn_mesh *>(cm);
+    if (m->a.cell_wide || m->np == 0) {
+        *cells = static_cast<const uint64_t *>(m->a.cells);
+        return SN_OK;
+    }
+    if (!m->cells64) {
+        sn_status r = pool_alloc((void **)&m->cells64, sizeof(uint64_t) * (size_t)m->np, m->pool, m->stream,
+                                 "64-bit cell codes");
+        if (r != SN_OK) return r;
+        cudaError_t e = sn::launch_cells64(m->a, m->np, m->cells64, m->stream);
+        if (e != cudaSuccess) {
+            pool_free(m->cells64, m->stream);
+            m->cells64 = nullptr;
+            return cuda_fail(e, "64-bit cell codes");
+        }
+    }
+    *cells = m->cells64;
     return SN_OK;
 }
 
@@ -1079,7 +1108,7 @@ void sn_free(sn_mesh *m)
     if (m->copied && cudaStreamWaitEvent(m->stream, m->copied, 0) != cudaSuccess) cudaGetLastError();
     void *ps[] = {m->a.points,    m->a.offsets,   m->a.cells, m->a.quads, m->a.quad_labels, m->a.sten_off,
                   m->a.sten_ids,  m->a.face_mask, m->a.meta,  m->a.nbr,   m->a.nbrp,        m->a.lut_x,
-                  m->smooth_scratch, m->tris};
+                  m->smooth_scratch, m->tris, m->cells64};
     for (void *p : ps) {
         const char *c = static_cast<const char *>(p);
         if (m->arena && c >= m->arena && c < m->arena + m->arena_bytes) continue; // part of the arena

@@ -102,6 +102,24 @@ __device__ __forceinline__ void store_record(const MeshArrays &m, int32_t id, ui
     m.nbr[id] = make_uint2((uint32_t)r, (uint32_t)(r >> 32));
 }
 
+// The generating cell of point id (coordinates + 1, each in [0, n]) in the mesh's cell layout.
+__device__ __forceinline__ void store_cell(const MeshArrays &m, int64_t id, uint32_t x1, uint32_t y1, uint32_t z1)
+{
+    if (m.cell_wide)
+        static_cast<uint64_t *>(m.cells)[id] = (uint64_t)x1 | ((uint64_t)y1 << 21) | ((uint64_t)z1 << 42);
+    else
+        static_cast<uint32_t *>(m.cells)[id] = x1 | (y1 << m.cell_sy) | (z1 << m.cell_sz);
+}
+__device__ __forceinline__ uint3 load_cell(const void *cells, int wide, int sy, int sz, int64_t i)
+{
+    if (wide) {
+        const uint64_t c = static_cast<const uint64_t *>(cells)[i], m21 = (1ull << 21) - 1ull;
+        return make_uint3((uint32_t)(c & m21), (uint32_t)((c >> 21) & m21), (uint32_t)(c >> 42));
+    }
+    const uint32_t c = static_cast<const uint32_t *>(cells)[i];
+    return make_uint3(c & ((1u << sy) - 1u), (c >> sy) & ((1u << (sz - sy)) - 1u), c >> sz);
+}
+
 // A decoded neighbour record: -x/+x presence (0/1) and the four id distances.
 struct NbrDist {
     uint32_t mx, px, dmy, dpy, dmz, dpz;

@@ -263,7 +263,7 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
             if (id < 0 || id >= NP) continue;
             const uint32_t lt = (1u << b) - 1u;
             const int64_t cy = c0 - 1 + lr;
-            m.cells[id] = (uint64_t)p | ((uint64_t)(cy + 1) << 21) | ((uint64_t)czc << 42);
+            store_cell(m, id, (uint32_t)p, (uint32_t)(cy + 1), (uint32_t)czc);
             const int64_t so = sSoff[lr] + sDpre[lr * W + w] + (e & 255u);
             m.face_mask[id] = (uint8_t)mask;
             m.sten_off[id] = so;

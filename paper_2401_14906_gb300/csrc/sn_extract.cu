@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 3) k_emit(const T *__restrict
             pt[0] = m.lut_x[cx + 1].x;
             pt[1] = m.lut_y[cy + 1].x;
             pt[2] = m.lut_z[cz + 1].x;
-            m.cells[id] = (uint64_t)(cx + 1) | ((uint64_t)(cy + 1) << 21) | ((uint64_t)(cz + 1) << 42);
+            store_cell(m, id, (uint32_t)(cx + 1), (uint32_t)(cy + 1), (uint32_t)(cz + 1));
             uint32_t mask = 0;
             int64_t so = sbase + sh.dpre[wp][wl];
 #pragma unroll

@@ -88,7 +88,9 @@ enum RecMode { REC_PACKED = 0, REC_WIDE = 1, REC_CSR = 2, REC_SPLIT = 3 };
 struct MeshArrays {
     float *points;       // [np][3] world coordinates
     float *offsets;      // [np][3] cell-local displacement, voxel units
-    uint64_t *cells;     // [np] packed (cx+1) | (cy+1)<<21 | (cz+1)<<42
+    void *cells;         // [np] packed generating cell: uint64 (cx+1) | (cy+1)<<21 | (cz+1)<<42 when cell_wide,
+                         // else uint32 (cx+1) | (cy+1)<<cell_sy | (cz+1)<<cell_sz (the extents fit 32 bits)
+    int cell_wide, cell_sy, cell_sz;
     int32_t *quads;      // [nq][4]
     void *quad_labels;   // [nq][2] label type
     int64_t *sten_off;   // [np+1]
@@ -246,6 +248,8 @@ cudaError_t launch_learn_adamw(float *params, float *m1, float *m2, const float 
 cudaError_t launch_triangulate(const MeshArrays &m, int64_t np, int64_t nq, int method, int32_t *tris,
                                cudaStream_t st);
 cudaError_t launch_centres(const MeshArrays &m, int64_t np, cudaStream_t st);
+// the cell codes of a mesh with 32-bit codes, as (cx+1) | (cy+1)<<21 | (cz+1)<<42 (sn_smooth.cu)
+cudaError_t launch_cells64(const MeshArrays &m, int64_t np, uint64_t *out, cudaStream_t st);
 
 // detail message returned by sn_last_error() on this thread (sn_api.cu)
 void set_last_error(const char *msg);

@@ -18,14 +18,13 @@ __global__ void __launch_bounds__(256) k_centres(MeshArrays m, int64_t np)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
-    const uint64_t c = m.cells[i];
-    const uint64_t m21 = (1ull << 21) - 1ull;
+    const uint3 c = load_cell(m.cells, m.cell_wide, m.cell_sy, m.cell_sz, i);
     m.offsets[3 * i + 0] = 0.f;
     m.offsets[3 * i + 1] = 0.f;
     m.offsets[3 * i + 2] = 0.f;
-    m.points[3 * i + 0] = m.lut_x[c & m21].x;
-    m.points[3 * i + 1] = m.lut_y[(c >> 21) & m21].x;
-    m.points[3 * i + 2] = m.lut_z[(c >> 42) & m21].x;
+    m.points[3 * i + 0] = m.lut_x[c.x].x;
+    m.points[3 * i + 1] = m.lut_y[c.y].x;
+    m.points[3 * i + 2] = m.lut_z[c.z].x;
 }
 
 // Launch t of the sweeps of many meshes: CTA b works on block b - block_start[i]
@@ -57,6 +56,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_smooth_batch(const SmoothBatc
     a.fmask = mp.m.face_mask;
     a.meta = mp.m.meta;
     a.cells = mp.m.cells;
+    a.cell_wide = mp.m.cell_wide;
+    a.cell_sy = mp.m.cell_sy;
+    a.cell_sz = mp.m.cell_sz;
     a.lut_x = mp.m.lut_x;
     a.lut_y = mp.m.lut_y;
     a.lut_z = mp.m.lut_z;
@@ -73,17 +75,24 @@ __global__ void __launch_bounds__(kSweepThreads) k_smooth_batch(const SmoothBatc
     sweep_block<false, FUSED>(a, (b - block_start[lo]) * (uint32_t)kSweepPoints);
 }
 
+__global__ void __launch_bounds__(256) k_cells64(MeshArrays m, int64_t np, uint64_t *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const uint3 c = load_cell(m.cells, m.cell_wide, m.cell_sy, m.cell_sz, i);
+    out[i] = (uint64_t)c.x | ((uint64_t)c.y << 21) | ((uint64_t)c.z << 42);
+}
+
 // world positions from the offsets in `o`
 __global__ void __launch_bounds__(256) k_world(MeshArrays m, const float *o, int64_t np, float spx, float spy,
                                                float spz)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
-    const uint64_t c = m.cells[i];
-    const uint64_t m21 = (1ull << 21) - 1ull;
-    m.points[3 * i + 0] = world(m.lut_x[c & m21], spx, o[3 * i + 0]);
-    m.points[3 * i + 1] = world(m.lut_y[(c >> 21) & m21], spy, o[3 * i + 1]);
-    m.points[3 * i + 2] = world(m.lut_z[(c >> 42) & m21], spz, o[3 * i + 2]);
+    const uint3 c = load_cell(m.cells, m.cell_wide, m.cell_sy, m.cell_sz, i);
+    m.points[3 * i + 0] = world(m.lut_x[c.x], spx, o[3 * i + 0]);
+    m.points[3 * i + 1] = world(m.lut_y[c.y], spy, o[3 * i + 1]);
+    m.points[3 * i + 2] = world(m.lut_z[c.z], spz, o[3 * i + 2]);
 }
 
 // Launches sweep `a` on st; `dependent`: as a programmatic dependent of the
@@ -109,6 +118,13 @@ cudaError_t launch_sweep(const SweepArgs &a, unsigned blocks, bool dependent, cu
 }
 
 } // namespace
+
+cudaError_t launch_cells64(const MeshArrays &m, int64_t np, uint64_t *out, cudaStream_t st)
+{
+    if (np == 0) return cudaSuccess;
+    k_cells64<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(m, np, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_centres(const MeshArrays &m, int64_t np, cudaStream_t st)
 {
@@ -136,6 +152,9 @@ cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float
     a.fmask = m.face_mask;
     a.meta = m.meta;
     a.cells = m.cells;
+    a.cell_wide = m.cell_wide;
+    a.cell_sy = m.cell_sy;
+    a.cell_sz = m.cell_sz;
     a.lut_x = m.lut_x;
     a.lut_y = m.lut_y;
     a.lut_z = m.lut_z;
@@ -199,6 +218,9 @@ cudaError_t launch_smooth_from(const MeshArrays &m, int64_t np, int iterations, 
     a.fmask = m.face_mask;
     a.meta = m.meta;
     a.cells = m.cells;
+    a.cell_wide = m.cell_wide;
+    a.cell_sy = m.cell_sy;
+    a.cell_sz = m.cell_sz;
     a.lut_x = m.lut_x;
     a.lut_y = m.lut_y;
     a.lut_z = m.lut_z;

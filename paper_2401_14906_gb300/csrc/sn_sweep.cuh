@@ -42,7 +42,8 @@ struct SweepArgs {
     const int32_t *sids;
     const uint8_t *fmask;
     const int32_t *meta;
-    const uint64_t *cells;
+    const void *cells;
+    int cell_wide, cell_sy, cell_sz;
     const float2 *lut_x, *lut_y, *lut_z;
     float *points;
     int64_t np;
@@ -158,12 +159,11 @@ __device__ __forceinline__ void sweep_point(const SweepArgs &a, uint32_t i, floa
     dst[1] = ny;
     dst[2] = nz;
     if (a.last) {
-        const uint64_t c = a.cells[i];
-        const uint64_t m21 = (1ull << 21) - 1ull;
+        const uint3 c = load_cell(a.cells, a.cell_wide, a.cell_sy, a.cell_sz, i);
         float *pt = a.points + 3ull * i;
-        pt[0] = world(a.lut_x[c & m21], a.spx, nx);
-        pt[1] = world(a.lut_y[(c >> 21) & m21], a.spy, ny);
-        pt[2] = world(a.lut_z[(c >> 42) & m21], a.spz, nz);
+        pt[0] = world(a.lut_x[c.x], a.spx, nx);
+        pt[1] = world(a.lut_y[c.y], a.spy, ny);
+        pt[2] = world(a.lut_z[c.z], a.spz, nz);
     }
 }
 
@@ -191,12 +191,11 @@ template <bool COH> __device__ __forceinline__ void sweep_point_csr(const SweepA
     dst[1] = ny;
     dst[2] = nz;
     if (a.last) {
-        const uint64_t c = a.cells[i];
-        const uint64_t m21 = (1ull << 21) - 1ull;
+        const uint3 c = load_cell(a.cells, a.cell_wide, a.cell_sy, a.cell_sz, i);
         float *pt = a.points + 3ull * i;
-        pt[0] = world(a.lut_x[c & m21], a.spx, nx);
-        pt[1] = world(a.lut_y[(c >> 21) & m21], a.spy, ny);
-        pt[2] = world(a.lut_z[(c >> 42) & m21], a.spz, nz);
+        pt[0] = world(a.lut_x[c.x], a.spx, nx);
+        pt[1] = world(a.lut_y[c.y], a.spy, ny);
+        pt[2] = world(a.lut_z[c.z], a.spz, nz);
     }
 }
 
