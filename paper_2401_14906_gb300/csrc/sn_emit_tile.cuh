@@ -13,7 +13,10 @@ namespace dev {
 #endif
 constexpr int kTileRows = SN_EMIT_ROWS; // cell rows per tile when fixed (SN_EMIT_ROWS_FIXED)
 constexpr int kTileMaxW = 64;  // rows of up to 2047 cells; wider rows use the per-row kernel
-constexpr int kListCap = 2048; // entries of the tile's position list (one chunk of points or quads)
+#ifndef SN_EMIT_LISTCAP
+#define SN_EMIT_LISTCAP 2048
+#endif
+constexpr int kListCap = SN_EMIT_LISTCAP; // entries of the tile's position list (one chunk of points or quads)
 
 // shared-memory carve-up, in 4-byte words; every array starts on 16 bytes
 struct TileSmem {
