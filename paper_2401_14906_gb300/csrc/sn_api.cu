@@ -628,7 +628,7 @@ sn_status job_emit(ExtractJob &j, cudaStream_t st, int emit_rows, bool batched =
         if ((e = cudaMemsetAsync(m->a.meta, 0, sizeof(int32_t) * 4, st)) != cudaSuccess)
             return cuda_fail(e, "mesh meta");
     }
-    e = sn::launch_emit_tile(j.type, j.dlabels, j.cls, j.g, j.s, m->a, j.dtot, st, emit_rows);
+    e = sn::launch_emit_tile(j.type, j.dlabels, j.cls, j.g, j.s, m->a, j.dtot, st, emit_rows, m->np + m->nq);
     if (e == cudaErrorNotSupported) {
         cudaGetLastError();
         e = sn::launch_emit(j.type, j.dlabels, j.cls, j.g, j.s, m->a, j.dtot, st);

@@ -43,7 +43,8 @@ cudaError_t emit_tile_t(const void *labels, const Classifier &c, const Geometry 
 {
     // one fixed limit (the largest tile any launch may use), so that launches captured
     // into one graph with different tile shapes all stay within it
-    static const int kMaxSmem = (int)(sizeof(uint32_t) * (size_t)TileSmem(kEmitMaxRows, kTileMaxW, kTileMaxW).total);
+    static const int kMaxSmem =
+        (int)(sizeof(uint32_t) * (size_t)TileSmem(kEmitMaxRows, kTileMaxW, kTileMaxW, kListCapMax).total);
     if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
     static std::atomic<uint64_t> done{0};
     cudaError_t e = smem_limit_once(k_emit_tile<T, MODE>, kMaxSmem, done);
@@ -67,14 +68,14 @@ cudaError_t emit_tile_m(int type, const void *labels, const Classifier &c, const
 // whose shared memory lets five tiles of kEmitThreads threads stay resident per
 // SM (228 KB per SM, 1 KB of it reserved per CTA).  Dense maps (many points per
 // row) gain from the residency; sparse ones from the longer tiles.
-int default_rows(int W, int WS)
+int default_rows(int W, int WS, int lcap)
 {
 #ifdef SN_EMIT_ROWS_FIXED
     return kTileRows;
 #else
     constexpr int kBudget = 228 * 1024 / 5 - 1024;
     for (int r = kEmitMaxRows; r > 8; r -= 4)
-        if ((int)sizeof(uint32_t) * TileSmem(r, W, WS).total <= kBudget) return r;
+        if ((int)sizeof(uint32_t) * TileSmem(r, W, WS, lcap).total <= kBudget) return r;
     return 8;
 #endif
 }
@@ -82,17 +83,21 @@ int default_rows(int W, int WS)
 } // namespace
 
 cudaError_t launch_emit_tile(int type, const void *labels, const Classifier &c, const Geometry &g,
-                             const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st, int rows)
+                             const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st, int rows,
+                             int64_t items)
 {
     if (g.W > kTileMaxW || g.nz + 1 > 65535) return cudaErrorNotSupported;
     if (rows < 0 || rows > kEmitMaxRows) return cudaErrorInvalidValue;
     TileGeom tg;
-    tg.ty = rows ? rows : default_rows((int)g.W, (int)g.WS);
+    // position list: chunks of about a 20-row tile's points or quads, 1024 to 4096 entries
+    const double per_row = (double)items / (double)((g.ny + 1) * (g.nz + 1));
+    tg.lcap = per_row > 200.0 ? 4096 : per_row > 50.0 ? 2048 : 1024;
+    tg.ty = rows ? rows : default_rows((int)g.W, (int)g.WS, tg.lcap);
     tg.W = (int)g.W;
     tg.WS = (int)g.WS;
     tg.ns = 3 * (tg.ty + 2);
     tg.wdiv = (0x100000000ull + (uint64_t)g.W - 1) / (uint64_t)g.W;
-    const size_t smem = sizeof(uint32_t) * (size_t)TileSmem(tg.ty, tg.W, tg.WS).total;
+    const size_t smem = sizeof(uint32_t) * (size_t)TileSmem(tg.ty, tg.W, tg.WS, tg.lcap).total;
     ProfScope ps("k_emit_tile", st);
     if (c.mode == CLASS_ALL) return emit_tile_m<CLASS_ALL>(type, labels, c, g, s, m, tot, tg, smem, st);
     if (c.mode == CLASS_BITMAP) return emit_tile_m<CLASS_BITMAP>(type, labels, c, g, s, m, tot, tg, smem, st);

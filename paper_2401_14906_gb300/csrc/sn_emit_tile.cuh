@@ -13,16 +13,13 @@ namespace dev {
 #endif
 constexpr int kTileRows = SN_EMIT_ROWS; // cell rows per tile when fixed (SN_EMIT_ROWS_FIXED)
 constexpr int kTileMaxW = 64;  // rows of up to 2047 cells; wider rows use the per-row kernel
-#ifndef SN_EMIT_LISTCAP
-#define SN_EMIT_LISTCAP 2048
-#endif
-constexpr int kListCap = SN_EMIT_LISTCAP; // entries of the tile's position list (one chunk of points or quads)
+constexpr int kListCapMax = 4096; // entries of the tile's position list (one chunk of points or quads), at most
 
 // shared-memory carve-up, in 4-byte words; every array starts on 16 bytes
 struct TileSmem {
     int bar, P, planes, wb, dpre, qpre, soff, qoff, list, total;
     __host__ __device__ static int up4(int v) { return (v + 3) & ~3; }
-    __host__ __device__ TileSmem(int ty, int W, int WS)
+    __host__ __device__ TileSmem(int ty, int W, int WS, int lcap)
     {
         const int ns = 3 * (ty + 2);
         bar = 0;                               // one mbarrier, padded to 16 bytes
@@ -33,8 +30,8 @@ struct TileSmem {
         qpre = dpre + up4((ty * W + 1) / 2);   // [ty][W] uint16 quads before the word
         soff = qpre + up4((ty * W + 1) / 2);   // [ty] int64 first stencil entry of the row
         qoff = soff + 2 * ty;                  // [ty] int64 first quad of the sample row
-        list = qoff + 2 * ty;                  // [kListCap] positions of one chunk of points or quads
-        total = list + kListCap;
+        list = qoff + 2 * ty;                  // [lcap] positions of one chunk of points or quads
+        total = list + lcap;
     }
 };
 
@@ -45,7 +42,7 @@ struct TileSmem {
 // wait gave up; the copies may then still be in flight.
 //
 // After staging, the tile's points (and then its quads) are written in id
-// order in chunks of kListCap: for each chunk, one thread per (row, word)
+// order in chunks of tg.lcap: for each chunk, one thread per (row, word)
 // lists the positions of the word's points that fall in the chunk (a loop over
 // the word's set bits), and then one thread per id takes its position from the
 // list -- consecutive threads write consecutive ids.  The list entry of a point
@@ -69,7 +66,8 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
     const int64_t czc = by;     // cz + 1
     const int64_t cz = czc - 1;
     const int n = (int)(ny1 - c0 < TY ? ny1 - c0 : TY);
-    const TileSmem L(TY, W, WS);
+    const TileSmem L(TY, W, WS, tg.lcap);
+    const int32_t LC = tg.lcap;
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.bar);
     uint32_t *sP = sm + L.P;
     uint32_t *sPl = sm + L.planes;
@@ -232,8 +230,8 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
     const int last = slot_of(1, n - 1);
     const int32_t pbase = sWB[slot_of(1, 0) * W];
     const int32_t npts = sWB[last * W + (W - 1)] + __popc(sP[last * WS + (W - 1)]) - pbase;
-    for (int32_t lo = 0; lo < npts; lo += kListCap) {
-        const int32_t hi = npts - lo < kListCap ? npts : lo + kListCap;
+    for (int32_t lo = 0; lo < npts; lo += LC) {
+        const int32_t hi = npts - lo < LC ? npts : lo + LC;
         __syncthreads(); // the previous chunk's list is read no more
         for (int it = tid; it < n * W; it += nthr) {
             const int lr = (int)(((uint64_t)(uint32_t)it * tg.wdiv) >> 32), w = it - lr * W;
@@ -295,8 +293,8 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
     const int32_t nqt = (int32_t)(sQoff[n - 1] - qbase) + (int32_t)sQpre[(n - 1) * W + (W - 1)] +
                         __popc(PL(0, 0, n - 1)[W - 1]) + __popc(PL(0, 1, n - 1)[W - 1]) +
                         __popc(PL(0, 2, n - 1)[W - 1]);
-    for (int32_t lo = 0; lo < nqt; lo += kListCap) {
-        const int32_t hi = nqt - lo < kListCap ? nqt : lo + kListCap;
+    for (int32_t lo = 0; lo < nqt; lo += LC) {
+        const int32_t hi = nqt - lo < LC ? nqt : lo + LC;
         __syncthreads();
         for (int it = lr_first * W + tid; it < n * W; it += nthr) {
             const int lr = (int)(((uint64_t)(uint32_t)it * tg.wdiv) >> 32), w = it - lr * W;

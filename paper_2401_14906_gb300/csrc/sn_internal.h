@@ -123,6 +123,7 @@ struct TileGeom {
     int W, WS;     // words per row, row stride in words
     int ns;        // staged point-plane rows: 3 * (ty + 2)
     uint64_t wdiv; // ceil(2^32 / W): it / W == (it * wdiv) >> 32
+    int lcap;      // entries of the position list (points or quads listed per chunk)
 };
 
 constexpr int kEmitMaxRows = 32;
@@ -175,10 +176,11 @@ cudaError_t launch_emit(int type, const void *labels, const Classifier &c, const
 
 // Pass 4 over tiles of cell rows (sn_emit.cu); cudaErrorNotSupported for rows too
 // wide for its shared-memory staging (launch_emit is used then).  rows = cell
-// rows per tile, 1..kEmitMaxRows (0: the default).
+// rows per tile, 1..kEmitMaxRows (0: the default); items = points + quads of the
+// mesh, which sizes the tile's position list.
 cudaError_t launch_emit_tile(int type, const void *labels, const Classifier &c, const Geometry &g,
                              const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st,
-                             int rows = 0);
+                             int rows = 0, int64_t items = 0);
 
 // Many meshes' cell-centre tables and meta words in one launch, and their last
 // stencil offsets (sten_tail = *sten_total) in another (sn_extract.cu).
