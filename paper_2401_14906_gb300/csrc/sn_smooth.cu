@@ -1,5 +1,7 @@
 // sn_smooth.cu -- constrained Laplacian smoothing (Sec. 2.2 Eq. 1, Sec. 2.4) of one
 // mesh: one launch per Jacobi sweep (the sweep itself is in sn_sweep.cuh).
+#include <atomic>
+
 #include "sn_sweep.cuh"
 
 namespace sn {
@@ -72,6 +74,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_smooth_batch(const SmoothBatc
     a.first = t == 0;
     a.last = t == launches - 1;
     a.sphere = sphere;
+    a.ahead = 0;
     sweep_block<false, FUSED>(a, (b - block_start[lo]) * (uint32_t)kSweepPoints);
 }
 
@@ -97,6 +100,25 @@ __global__ void __launch_bounds__(256) k_world(MeshArrays m, const float *o, int
 
 // Launches sweep `a` on st; `dependent`: as a programmatic dependent of the
 // kernel before it on the stream (the previous sweep), see sweep_block.
+// resident CTAs of a sweep launch on the current device: the prefetch distance
+uint32_t sweep_wave()
+{
+    static std::atomic<int> wave{0};
+    int w = wave.load();
+    if (w == 0) {
+        int dev = 0, sms = 0, per = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_smooth<false>, kSweepThreads, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        w = sms * (per > 0 ? per : 1);
+        wave.store(w);
+    }
+    return (uint32_t)w;
+}
+
 cudaError_t launch_sweep(const SweepArgs &a, unsigned blocks, bool dependent, cudaStream_t st)
 {
     if (!dependent) {
@@ -166,6 +188,7 @@ cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float
     a.spx = (float)spacing[0];
     a.spy = (float)spacing[1];
     a.spz = (float)spacing[2];
+    a.ahead = sweep_wave();
     // sweeps 1 and 2 run as one launch (unless the sweeps read the CSR stencil);
     // the first destination is chosen so that the last launch writes m.offsets
     // (the first launch reads no offsets)
@@ -232,6 +255,7 @@ cudaError_t launch_smooth_from(const MeshArrays &m, int64_t np, int iterations, 
     a.spx = (float)spacing[0];
     a.spy = (float)spacing[1];
     a.spz = (float)spacing[2];
+    a.ahead = sweep_wave();
     a.first = 0;
     float *src = start;
     float *dst = start == m.offsets ? scratch : m.offsets;

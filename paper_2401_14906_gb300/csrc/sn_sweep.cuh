@@ -52,6 +52,7 @@ struct SweepArgs {
     int first;       // sweep 1 (all offsets are zero before it), or sweeps 1 and 2 at once (FUSED)
     int last;        // the last sweep: also write world coordinates
     int sphere;      // constrain |o| <= h instead of |o_a| <= h per axis
+    uint32_t ahead;  // blocks between a block and the one whose streamed inputs it prefetches into L2 (0: none)
     int rec;         // RecMode of the mesh
     int by, bz;      // field widths (REC_PACKED)
 };
@@ -199,6 +200,9 @@ template <bool COH> __device__ __forceinline__ void sweep_point_csr(const SweepA
     }
 }
 
+#ifndef SN_SWEEP_PREFETCH
+#define SN_SWEEP_PREFETCH 1
+#endif
 #ifndef SN_SWEEP_THREADS
 #define SN_SWEEP_THREADS 256
 #endif
@@ -225,6 +229,23 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, uint32_t base)
 {
     const uint64_t np = (uint64_t)a.np;
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // Prefetch into L2 the streamed inputs (neighbour records, and the own
+    // offsets of sweeps that read them) of the block `ahead` blocks later,
+    // which runs about one wave of resident CTAs after this one: its loads then
+    // come from L2.  Records and offsets of a block are contiguous and start on
+    // 4 KB boundaries; the sizes are cut to whole 16-byte units at the array end.
+    if (SN_SWEEP_PREFETCH && a.ahead && threadIdx.x == 0) {
+        const uint64_t nb0 = (uint64_t)base + (uint64_t)a.ahead * kSweepPoints;
+        if (nb0 < np) {
+            const uint64_t n = np - nb0 < (uint64_t)kSweepPoints ? np - nb0 : (uint64_t)kSweepPoints;
+            const uint32_t rb = (uint32_t)((n * 8ull) & ~15ull);
+            if (a.rec != REC_CSR && rb)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.nbr + nb0), "r"(rb) : "memory");
+            const uint32_t ob = (uint32_t)((n * 12ull) & ~15ull);
+            if (!a.first && ob)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.oin + 3ull * nb0), "r"(ob) : "memory");
+        }
+    }
     if (a.rec == REC_CSR) {
         asm volatile("griddepcontrol.wait;" ::: "memory");
 #pragma unroll
