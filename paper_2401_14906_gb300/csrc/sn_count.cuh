@@ -22,6 +22,10 @@ namespace dev {
 #define SN_COUNT_SLOTS 3
 #endif
 constexpr int kCountSlots = SN_COUNT_SLOTS; // label slices in flight per tile (a ring of TMA destinations)
+#ifndef SN_COUNT_PREFETCH
+#define SN_COUNT_PREFETCH 2
+#endif
+constexpr int kCountPrefetch = SN_COUNT_PREFETCH; // slices beyond the copied one brought into L2 ahead (0: none)
 static_assert(kCountSlots >= 3 && kCountSlots <= 4, "the header holds four mbarriers before the row counters");
 #ifndef SN_COUNT_MAX_TY
 #define SN_COUNT_MAX_TY 32
@@ -239,6 +243,12 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_expect_tx(&bars[slot], slice_bytes);
                 bulk_load(dst, src, slice_bytes, &bars[slot]);
+                // and bring the slice kCountPrefetch further on into L2, so that its copy,
+                // issued kCountPrefetch steps later, is served from L2
+                if (kCountPrefetch && kk + kCountPrefetch < k_ld_end)
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src + (int64_t)kCountPrefetch * ny * lp),
+                                 "r"(slice_bytes)
+                                 : "memory");
             }
         } else {
             const int64_t n = (int64_t)rows_ld * lp;

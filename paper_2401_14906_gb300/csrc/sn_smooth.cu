@@ -100,23 +100,30 @@ __global__ void __launch_bounds__(256) k_world(MeshArrays m, const float *o, int
 
 // Launches sweep `a` on st; `dependent`: as a programmatic dependent of the
 // kernel before it on the stream (the previous sweep), see sweep_block.
-// resident CTAs of a sweep launch on the current device: the prefetch distance
-uint32_t sweep_wave()
+// The prefetch distance of a sweep over np points: the resident CTAs of a
+// sweep launch on the current device, or 0 (no prefetch) when the sweep's
+// offsets and records fit in L2 anyway (the prefetches then only cost issue
+// slots).
+uint32_t sweep_ahead(int64_t np)
 {
     static std::atomic<int> wave{0};
+    static std::atomic<int64_t> l2{0};
     int w = wave.load();
     if (w == 0) {
-        int dev = 0, sms = 0, per = 0;
+        int dev = 0, sms = 0, per = 0, l2b = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&l2b, cudaDevAttrL2CacheSize, dev) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_smooth<false>, kSweepThreads, 0) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
+        l2.store(l2b);
         w = sms * (per > 0 ? per : 1);
         wave.store(w);
     }
-    return (uint32_t)w;
+    // two offset buffers and the records: 32 bytes per point
+    return np * 32 > l2.load() ? (uint32_t)w : 0u;
 }
 
 cudaError_t launch_sweep(const SweepArgs &a, unsigned blocks, bool dependent, cudaStream_t st)
@@ -188,7 +195,7 @@ cudaError_t launch_smooth(const MeshArrays &m, int64_t np, int iterations, float
     a.spx = (float)spacing[0];
     a.spy = (float)spacing[1];
     a.spz = (float)spacing[2];
-    a.ahead = sweep_wave();
+    a.ahead = sweep_ahead(np);
     // sweeps 1 and 2 run as one launch (unless the sweeps read the CSR stencil);
     // the first destination is chosen so that the last launch writes m.offsets
     // (the first launch reads no offsets)
@@ -255,7 +262,7 @@ cudaError_t launch_smooth_from(const MeshArrays &m, int64_t np, int iterations, 
     a.spx = (float)spacing[0];
     a.spy = (float)spacing[1];
     a.spz = (float)spacing[2];
-    a.ahead = sweep_wave();
+    a.ahead = sweep_ahead(np);
     a.first = 0;
     float *src = start;
     float *dst = start == m.offsets ? scratch : m.offsets;
