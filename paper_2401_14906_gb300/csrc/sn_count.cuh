@@ -23,7 +23,7 @@ namespace dev {
 #endif
 constexpr int kCountSlots = SN_COUNT_SLOTS; // label slices in flight per tile (a ring of TMA destinations)
 #ifndef SN_COUNT_PREFETCH
-#define SN_COUNT_PREFETCH 2
+#define SN_COUNT_PREFETCH 0
 #endif
 constexpr int kCountPrefetch = SN_COUNT_PREFETCH; // slices beyond the copied one brought into L2 ahead (0: none)
 static_assert(kCountSlots >= 3 && kCountSlots <= 4, "the header holds four mbarriers before the row counters");
