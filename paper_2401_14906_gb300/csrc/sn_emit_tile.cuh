@@ -13,6 +13,9 @@ namespace dev {
 #endif
 constexpr int kTileRows = SN_EMIT_ROWS; // cell rows per tile when fixed (SN_EMIT_ROWS_FIXED)
 constexpr int kTileMaxW = 64;  // rows of up to 2047 cells; wider rows use the per-row kernel
+#ifndef SN_EMIT_LABEL_PREFETCH
+#define SN_EMIT_LABEL_PREFETCH 1
+#endif
 constexpr int kListCapMax = 4096; // entries of the tile's position list (one chunk of points or quads), at most
 
 // shared-memory carve-up, in 4-byte words; every array starts on 16 bytes
@@ -88,6 +91,21 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
         if (cy >= 0 && cz >= 0) work |= __ldcg(s.cntQ + cy + ny * cz) != 0;
     }
     if (!__syncthreads_or(work)) return true; // trimmed tile
+
+    // The label rows the quads read (sample rows c0-1 .. c0+n-1 of slices cz and
+    // cz+1) are one contiguous run per slice: bring them into L2 now, so that
+    // the quad phase, after the points, finds them there (rows on 16-byte
+    // boundaries only).
+    if (SN_EMIT_LABEL_PREFETCH && tid == 0 && cz >= 0 && (g.lp * (int64_t)sizeof(T)) % 16 == 0 &&
+        (reinterpret_cast<uintptr_t>(lab) & 15) == 0) {
+        const int64_t j0 = c0 - 1 < 0 ? 0 : c0 - 1, j1 = c0 - 1 + n < ny ? c0 - 1 + n : ny; // rows [j0, j1]
+        const uint32_t bytes = (uint32_t)((j1 - j0 + (j1 < ny ? 1 : 0)) * g.lp * (int64_t)sizeof(T));
+        for (int dk = 0; dk < 2 && bytes; ++dk)
+            if (cz + dk < nz)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lab + (j0 + ny * (cz + dk)) * g.lp),
+                             "r"(bytes)
+                             : "memory");
+    }
 
     // ---- staging: runs of rows copied by TMA; rows outside the volume are zeroed.
     // point-plane slot (dz, lr) = dz * (TY + 2) + lr + 1, dz 0/1/2 = slices cz-1/cz/cz+1, lr in [-1, TY]
