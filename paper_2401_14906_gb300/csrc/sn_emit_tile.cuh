@@ -14,7 +14,7 @@ namespace dev {
 constexpr int kTileRows = SN_EMIT_ROWS; // cell rows per tile when fixed (SN_EMIT_ROWS_FIXED)
 constexpr int kTileMaxW = 64;  // rows of up to 2047 cells; wider rows use the per-row kernel
 #ifndef SN_EMIT_LABEL_PREFETCH
-#define SN_EMIT_LABEL_PREFETCH 1
+#define SN_EMIT_LABEL_PREFETCH 0
 #endif
 constexpr int kListCapMax = 4096; // entries of the tile's position list (one chunk of points or quads), at most
 
