@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c3slab", "c5", "synthetic"])
+    p.add_argument("--slabs", action="store_true",
+                   help="split the map into z-slabs over the ranks (extract + smooth + count exchange + stitch "
+                        "on each rank's GPU; strong scaling) instead of running replicas")
     p.add_argument("--no-secondary", action="store_true",
                    help="skip the secondary objects (atlas map, batched maps, label sweep)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -786,8 +789,81 @@ def run_batch(args):
     return 0
 
 
+def run_slabs(args):
+    """z-slab decomposition of one map over the ranks (strong scaling): every rank extracts and smooths its
+    slab with ghost slices, the owned counts are exchanged (an allgather of three integers, NCCL under
+    torchrun), and each rank stitches its owned part with global ids on its GPU.  value = voxels of the map
+    / max over ranks of the time per step."""
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2401_14906_gb300 import build, slabs
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2401_14906_gb300 import sn
+    sn.load()
+    w = make_workload(args.workload)
+    nz = w.labels.shape[0]
+    p = slabs.slab_plan(nz, world, w.iterations)[rank]
+    lab = to_device(np.ascontiguousarray(w.labels[p["s0"]:p["s1"]]))
+    stream = torch.cuda.Stream()
+
+    def gather(vec):
+        if world == 1:
+            return np.asarray(vec, dtype=np.int64).reshape(1, 3)
+        return slabs.torch_allgather(vec)
+
+    def step():
+        part, _ = slabs.run_rank_device(lab, w.spacing, w.origin, w.iterations, w.relaxation, w.constraint, rank,
+                                        world, nz, gather, stream)
+        return part
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            part = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank == 0:
+        V = w.voxels
+        print(json.dumps({"metric": METRIC, "value": V * args.steps / (ms / 1e3) / 1e9, "unit": UNIT,
+                          "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+                          "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+                          "vs_baseline": None, "dtype": "u%d+f32" % (8 * w.labels.dtype.itemsize),
+                          "data": "synthetic",
+                          "config": workload_config(w, {"parallelism": "z-slabs over %d ranks" % world,
+                                                        "slab_rank0": [p["s0"], p["s1"]],
+                                                        "owned_points_rank0": int(part["stencil_offsets"].numel()),
+                                                        "timing": "CUDA events on rank 0's stream around K steps "
+                                                                  "(extract, smooth, count allgather, stitch), "
+                                                                  "max over ranks"})}))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
+    if args.slabs and args.impl != "reference":
+        return run_slabs(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.label_sweep:

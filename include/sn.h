@@ -406,6 +406,43 @@ void sn_profile_enable(int on);
 int sn_profile_read(sn_kernel_time *out, int cap, int reset);
 
 /*
+ * z-slab decomposition (Sec. 4.2 and 5: regions are left open at the volume's
+ * faces, so sub-volumes can be processed apart and their meshes joined).  A
+ * rank extracts and smooths a slab of sample slices with ghost slices on both
+ * sides; it owns the points of a run of cell slices and the quads whose first
+ * sample lies in a run of sample slices.  Points are ordered by cell slice and
+ * quads by first sample slice (Sec. 2.3), so both are contiguous ranges.
+ *
+ * sn_slab_part_of -- the owned ranges of mesh m: points of cell slices
+ *   cz in [cz_lo, cz_hi) and quads whose first sample slice k is in
+ *   [k_lo, k_hi), both in the slab's own coordinates (cz from -1).  Fills
+ *   `part` (host) with the first local id and count of points, quads and
+ *   stencil entries; waits for the mesh's stream.  Errors: SN_EINVAL, SN_ECUDA.
+ * sn_slab_stitch -- writes the owned quads, stencil offsets and stencil ids
+ *   with global ids: the ranks' owned counts, gathered and scanned in rank
+ *   order, give this rank's first global point and stencil entry; every id
+ *   (and every stencil offset) is then the local one shifted by the same
+ *   amount, halo neighbours included, since the slice below the owned run ends
+ *   the previous rank's range and the slice above starts the next one's.
+ *   quads: device int32 [n_quads][4]; stencil_offsets: device int64
+ *   [n_points]; stencil_ids: device int32 [n_stencil]; caller-owned.  The
+ *   owned points, offsets, cells and label pairs are the sub-ranges
+ *   [first_point, first_point + n_points) and [first_quad, ...) of the mesh's
+ *   own arrays.  Enqueued on `cuda_stream` after the mesh's stream.  Errors:
+ *   SN_EINVAL, SN_ECUDA.
+ */
+typedef struct {
+    int64_t first_point, n_points;
+    int64_t first_quad, n_quads;
+    int64_t first_stencil, n_stencil;
+} sn_slab_part;
+sn_status sn_slab_part_of(const sn_mesh *m, int64_t cz_lo, int64_t cz_hi, int64_t k_lo, int64_t k_hi,
+                          sn_slab_part *part);
+sn_status sn_slab_stitch(const sn_mesh *m, const sn_slab_part *part, int64_t global_first_point,
+                         int64_t global_first_stencil, int32_t *quads, int64_t *stencil_offsets,
+                         int32_t *stencil_ids, void *cuda_stream);
+
+/*
  * Failure injection for tests.  The paper has no counterpart (its Sec. 4 notes
  * that the full connectome exhausts memory; these calls make the library's own
  * failure paths fire on demand, with no GPU fault).  Each setting is

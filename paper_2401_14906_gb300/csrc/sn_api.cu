@@ -959,6 +959,63 @@ sn_status sn_mesh_record_bytes(const sn_mesh *m, int *bytes_per_point)
     return SN_OK;
 }
 
+sn_status sn_slab_part_of(const sn_mesh *m, int64_t cz_lo, int64_t cz_hi, int64_t k_lo, int64_t k_hi,
+                          sn_slab_part *part)
+{
+    g_last_error.clear();
+    if (!m || !part) return fail(SN_EINVAL, "mesh or part is NULL");
+    if (cz_hi < cz_lo || k_hi < k_lo) return fail(SN_EINVAL, "slice ranges need lo <= hi");
+    int64_t h[6] = {0, 0, 0, 0, 0, 0};
+    if (m->np > 0) {
+        int64_t *d = nullptr;
+        sn_status r = pool_alloc((void **)&d, sizeof(h), m->pool, m->stream, "slab bounds");
+        if (r != SN_OK) return r;
+        cudaError_t e = sn::launch_slab_bounds(m->a, m->np, m->nq, cz_lo, cz_hi, k_lo, k_hi, d, m->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, m->stream);
+        pool_free(d, m->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "slab bounds");
+    }
+    part->first_point = h[0];
+    part->n_points = h[1] - h[0];
+    part->first_quad = h[2];
+    part->n_quads = h[3] - h[2];
+    part->first_stencil = h[4];
+    part->n_stencil = h[5] - h[4];
+    return SN_OK;
+}
+
+sn_status sn_slab_stitch(const sn_mesh *m, const sn_slab_part *part, int64_t global_first_point,
+                         int64_t global_first_stencil, int32_t *quads, int64_t *stencil_offsets, int32_t *stencil_ids,
+                         void *cuda_stream)
+{
+    g_last_error.clear();
+    if (!m || !part) return fail(SN_EINVAL, "mesh or part is NULL");
+    const sn_slab_part &p = *part;
+    if (p.first_point < 0 || p.n_points < 0 || p.first_point + p.n_points > m->np || p.first_quad < 0 ||
+        p.n_quads < 0 || p.first_quad + p.n_quads > m->nq || p.first_stencil < 0 || p.n_stencil < 0 ||
+        p.first_stencil + p.n_stencil > m->ns)
+        return fail(SN_EINVAL, "part does not lie within the mesh");
+    if (global_first_point < 0 || global_first_stencil < 0) return fail(SN_EINVAL, "negative global offsets");
+    if ((p.n_quads && !quads) || (p.n_points && !stencil_offsets) || (p.n_stencil && !stencil_ids))
+        return fail(SN_EINVAL, "an output array is NULL");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaSuccess;
+    if (st != m->stream) { // after the mesh's work
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, m->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+        if (ev) cudaEventDestroy(ev);
+        if (e != cudaSuccess) return cuda_fail(e, "slab stitch");
+    }
+    e = sn::launch_slab_shift(m->a, p.first_point, p.n_points, p.first_quad, p.n_quads, p.first_stencil,
+                              p.n_stencil, global_first_point - p.first_point, global_first_stencil - p.first_stencil,
+                              quads, stencil_offsets, stencil_ids, st);
+    if (e != cudaSuccess) return cuda_fail(e, "slab stitch");
+    return SN_OK;
+}
+
 sn_status sn_mesh_copy_to_host(const sn_mesh *m, float *points, int32_t *quads, void *quad_labels,
                                int64_t *stencil_offsets, int32_t *stencil_ids, float *offsets)
 {

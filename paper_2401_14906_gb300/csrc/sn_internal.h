@@ -253,6 +253,15 @@ cudaError_t launch_centres(const MeshArrays &m, int64_t np, cudaStream_t st);
 // the cell codes of a mesh with 32-bit codes, as (cx+1) | (cy+1)<<21 | (cz+1)<<42 (sn_smooth.cu)
 cudaError_t launch_cells64(const MeshArrays &m, int64_t np, uint64_t *out, cudaStream_t st);
 
+// z-slab parts (sn_slab.cu): out[0..5] = first / end point, first / end quad,
+// first / end stencil entry of the owned ranges; the owned quads, stencil
+// offsets and ids shifted to global ids (dp for ids, ds for stencil offsets)
+cudaError_t launch_slab_bounds(const MeshArrays &m, int64_t np, int64_t nq, int64_t cz_lo, int64_t cz_hi,
+                               int64_t k_lo, int64_t k_hi, int64_t *out, cudaStream_t st);
+cudaError_t launch_slab_shift(const MeshArrays &m, int64_t first_point, int64_t n_points, int64_t first_quad,
+                              int64_t n_quads, int64_t first_stencil, int64_t n_stencil, int64_t dp, int64_t ds,
+                              int32_t *quads, int64_t *stencil_offsets, int32_t *stencil_ids, cudaStream_t st);
+
 // detail message returned by sn_last_error() on this thread (sn_api.cu)
 void set_last_error(const char *msg);
 

@@ -26,6 +26,10 @@ point ids then map to global canonical ids as follows:
 * the halo cell slice above it is the start of the next rank's range.
 
 A rank needs no data from its neighbours; the ghost slices are recomputed.
+Since both halo slices sit right next to the owned run in the canonical order,
+the whole id remap is one shift per rank (global = local - first owned local +
+first global), which sn_slab_stitch applies on the device (the `device_*`
+functions); `own`/`stitch` are the same steps on host arrays.
 """
 from __future__ import annotations
 
@@ -149,6 +153,87 @@ def torch_allgather(vec):
     out = [torch.empty_like(t) for _ in range(dist.get_world_size())]
     dist.all_gather(out, t)
     return np.stack([x.cpu().numpy() for x in out])
+
+
+# ------------------------------------------------------- device-resident path
+def device_part(sub_labels, spacing, sub_origin, p, iterations, relaxation, constraint, stream=None):
+    """Extract and smooth one rank's slab on its GPU and find its owned ranges (sn_slab_part_of).
+    Returns (mesh, part); the mesh stays on the device."""
+    from . import sn
+    s0 = p["s0"]
+    m = sn.sn_extract(sub_labels, spacing, sub_origin, stream=stream)
+    if iterations:
+        sn.sn_smooth(m, iterations, relaxation, constraint)
+    part = sn.sn_slab_part_of(m, p["c0"] - s0, p["c1"] - s0, p["k0"] - s0, p["k1"] - s0)
+    return m, part
+
+
+def device_stitch(m, part, first, z0, stream=None):
+    """The owned part of a slab mesh with global ids, as device tensors (sn_slab_stitch for the ids; the
+    other arrays are copies of contiguous ranges of the mesh).  `first` = (first global point, first
+    global quad, first global stencil entry) of this rank."""
+    import torch
+
+    from . import sn
+    quads, so, si = sn.sn_slab_stitch(m, part, first[0], first[2], stream=stream)
+    arr = sn.sn_mesh_device_arrays(m)
+    a, b = part.first_point, part.first_point + part.n_points
+    qa, qb = part.first_quad, part.first_quad + part.n_quads
+    cells = sn.sn_mesh_cells(m)[a:b].clone()
+    cells[:, 2] += z0
+    lab = arr["quad_labels"]
+    lab = lab.view({1: torch.uint8, 2: torch.int16, 4: torch.int32}[lab.element_size()])  # raw label bits
+    return {"points": arr["points"][a:b].clone(), "offsets": arr["offsets"][a:b].clone(), "cells": cells,
+            "quads": quads, "quad_labels": lab[qa:qb].clone(), "stencil_offsets": so,
+            "stencil_ids": si, "first_point": int(first[0]), "first_quad": int(first[1]),
+            "first_stencil": int(first[2])}
+
+
+def device_assemble(parts, totals):
+    """The global mesh (device tensors) from the ranks' device parts in rank order (one GPU)."""
+    import torch
+    out = {k: torch.cat([p[k] for p in parts]) for k in
+           ("points", "offsets", "cells", "quads", "quad_labels", "stencil_ids")}
+    out["stencil_offsets"] = torch.cat([p["stencil_offsets"] for p in parts] +
+                                       [torch.tensor([int(totals[2])], dtype=torch.int64, device="cuda")])
+    return out
+
+
+def run_rank_device(labels_dev, spacing, origin, iterations, relaxation, constraint, rank, world, nz,
+                    allgather, stream=None):
+    """One rank's share on its GPU with the slab labels already on the device: extract, smooth, count
+    exchange (`allgather`), stitch.  `labels_dev` holds sample slices [s0, s1) of the plan.  Returns the
+    owned part (device tensors) and the totals."""
+    p = slab_plan(nz, world, iterations)[rank]
+    sub_origin = (origin[0], origin[1], origin[2] + p["s0"] * spacing[2])
+    m, part = device_part(labels_dev, spacing, sub_origin, p, iterations, relaxation, constraint, stream)
+    counts_all = allgather(np.array([part.n_points, part.n_quads, part.n_stencil], dtype=np.int64))
+    ex, totals = exclusive_offsets(counts_all)
+    out = device_stitch(m, part, ex[rank], p["s0"], stream)
+    m.free()
+    return out, totals
+
+
+def emulate_device(labels, spacing, origin, iterations, relaxation, constraint, world):
+    """All ranks in one process on one GPU through the device path; returns the global mesh as host
+    arrays."""
+    nz = labels.shape[0]
+    plan = slab_plan(nz, world, iterations)
+    meshes = []
+    for p in plan:
+        sub_origin = (origin[0], origin[1], origin[2] + p["s0"] * spacing[2])
+        meshes.append(device_part(np.ascontiguousarray(labels[p["s0"]:p["s1"]]), spacing, sub_origin, p,
+                                  iterations, relaxation, constraint))
+    counts = np.array([[pt.n_points, pt.n_quads, pt.n_stencil] for _, pt in meshes], dtype=np.int64)
+    ex, totals = exclusive_offsets(counts)
+    parts = [device_stitch(m, pt, ex[r], plan[r]["s0"]) for r, (m, pt) in enumerate(meshes)]
+    for m, _ in meshes:
+        m.free()
+    out = device_assemble(parts, totals)
+    host = {k: v.cpu().numpy() for k, v in out.items()}
+    ldt = {1: np.uint8, 2: np.uint16, 4: np.uint32}[labels.dtype.itemsize]
+    host["quad_labels"] = host["quad_labels"].view(ldt)
+    return host
 
 
 def assemble(parts):

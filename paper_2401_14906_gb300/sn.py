@@ -33,6 +33,11 @@ class sn_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
+class sn_slab_part(ctypes.Structure):
+    _fields_ = [("first_point", ctypes.c_int64), ("n_points", ctypes.c_int64), ("first_quad", ctypes.c_int64),
+                ("n_quads", ctypes.c_int64), ("first_stencil", ctypes.c_int64), ("n_stencil", ctypes.c_int64)]
+
+
 # every symbol declared in include/sn.h, with its ctypes signature
 _P = ctypes.c_void_p
 _I64P = ctypes.POINTER(ctypes.c_int64)
@@ -81,6 +86,10 @@ SIGNATURES = {
     "sn_learner_step": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float]),
     "sn_profile_enable": (None, [ctypes.c_int]),
     "sn_profile_read": (ctypes.c_int, [ctypes.POINTER(sn_kernel_time), ctypes.c_int, ctypes.c_int]),
+    "sn_slab_part_of": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.POINTER(sn_slab_part)]),
+    "sn_slab_stitch": (ctypes.c_int, [_P, ctypes.POINTER(sn_slab_part), ctypes.c_int64, ctypes.c_int64, _P, _P, _P,
+                                      _P]),
     "sn_debug_set_spin_limit": (None, [ctypes.c_int]),
     "sn_debug_fail_allocation": (None, [ctypes.c_int64]),
     "sn_debug_set_point_limit": (None, [ctypes.c_int64]),
@@ -581,3 +590,24 @@ def sn_mesh_record_bytes(mesh) -> int:
     b = ctypes.c_int()
     _check(load().sn_mesh_record_bytes(mesh.handle, ctypes.byref(b)))
     return b.value
+
+
+# ------------------------------------------------------------------ z-slabs
+def sn_slab_part_of(mesh, cz_lo, cz_hi, k_lo, k_hi):
+    """Owned ranges of a slab mesh: points of cell slices [cz_lo, cz_hi), quads of first sample slices
+    [k_lo, k_hi) (slab coordinates).  Returns an sn_slab_part."""
+    part = sn_slab_part()
+    _check(load().sn_slab_part_of(mesh.handle, int(cz_lo), int(cz_hi), int(k_lo), int(k_hi), ctypes.byref(part)))
+    return part
+
+
+def sn_slab_stitch(mesh, part, global_first_point, global_first_stencil, stream=None):
+    """The owned quads, stencil offsets and stencil ids with global ids, as new device tensors."""
+    torch = _torch()
+    quads = torch.empty((part.n_quads, 4), dtype=torch.int32, device="cuda")
+    so = torch.empty(part.n_points, dtype=torch.int64, device="cuda")
+    si = torch.empty(part.n_stencil, dtype=torch.int32, device="cuda")
+    _check(load().sn_slab_stitch(mesh.handle, ctypes.byref(part), int(global_first_point), int(global_first_stencil),
+                                 ctypes.c_void_p(quads.data_ptr()), ctypes.c_void_p(so.data_ptr()),
+                                 ctypes.c_void_p(si.data_ptr()), ctypes.c_void_p(_stream_handle(stream, True))))
+    return quads, so, si
