@@ -345,18 +345,15 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
             // cell bits i (cx = i - 1) and i + 1 (cx = i)
             const int w0 = i >> 5, w1 = (i + 1) >> 5;
             const uint32_t lt0 = (1u << (i & 31)) - 1u, lt1 = (1u << ((i + 1) & 31)) - 1u;
-            int4 v;
-            int64_t d1;
-            if (ax == 0) {
-                v = make_int4(rank(smm, w1, lt1), rank(s0m, w1, lt1), rank(s00, w1, lt1), rank(sm0, w1, lt1));
-                d1 = 1;
-            } else if (ax == 1) {
-                v = make_int4(rank(s0m, w0, lt0), rank(s00, w0, lt0), rank(s00, w1, lt1), rank(s0m, w1, lt1));
-                d1 = g.lp;
-            } else {
-                v = make_int4(rank(sm0, w0, lt0), rank(sm0, w1, lt1), rank(s00, w1, lt1), rank(s00, w0, lt0));
-                d1 = g.lp * ny;
-            }
+            // the four cells of the edge without branching on its axis (the lanes of a warp mix axes):
+            //   x: (mm, 0m, 00, m0) at bit i+1;  y: (0m, 00, 00, 0m) at bits i, i, i+1, i+1;
+            //   z: (m0, m0, 00, 00) at bits i, i+1, i+1, i
+            const int sv0 = ax == 0 ? smm : ax == 1 ? s0m : sm0, sv1 = ax == 0 ? s0m : ax == 1 ? s00 : sm0;
+            const int sv3 = ax == 0 ? sm0 : ax == 1 ? s0m : s00;
+            const bool b0 = ax == 0, b1 = ax != 1, b3 = ax != 2;
+            const int4 v = make_int4(rank(sv0, b0 ? w1 : w0, b0 ? lt1 : lt0), rank(sv1, b1 ? w1 : w0, b1 ? lt1 : lt0),
+                                     rank(s00, w1, lt1), rank(sv3, b3 ? w1 : w0, b3 ? lt1 : lt0));
+            const int64_t d1 = ax == 0 ? 1 : ax == 1 ? g.lp : g.lp * ny;
             reinterpret_cast<int4 *>(m.quads)[q] = v;
             T *ql = reinterpret_cast<T *>(m.quad_labels) + 2 * q;
             ql[0] = (T)kappa<MODE>(c, ldlab(row, i));
