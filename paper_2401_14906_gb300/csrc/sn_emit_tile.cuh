@@ -290,15 +290,17 @@ __device__ __forceinline__ bool emit_tile(const T *__restrict__ lab, const Class
             int32_t *dst = m.sten_ids + so;
             if (mask & 1u) *dst++ = id - 1;
             if (mask & 2u) *dst++ = id + 1;
-            uint32_t dist[4] = {0u, 0u, 0u, 0u};
+            // the four -y/+y/-z/+z ranks are read whatever the mask (the staged rows are always there; the
+            // lanes of a warp have different masks), and stored where the face has a neighbour
+            uint32_t dist[4];
             const int nbs[4] = {slot_of(1, lr - 1), slot_of(1, lr + 1), slot_of(0, lr), slot_of(2, lr)};
 #pragma unroll
-            for (int f = 2; f < 6; ++f)
-                if ((mask >> f) & 1u) {
-                    const int32_t nb = rank(nbs[f - 2], w, lt);
-                    *dst++ = nb;
-                    dist[f - 2] = (uint32_t)(nb > id ? nb - id : id - nb);
-                }
+            for (int f = 2; f < 6; ++f) {
+                const int32_t nb = rank(nbs[f - 2], w, lt);
+                const bool has = (mask >> f) & 1u;
+                if (has) *dst++ = nb;
+                dist[f - 2] = has ? (uint32_t)(nb > id ? nb - id : id - nb) : 0u;
+            }
             store_record(m, id, mask, dist);
         }
     }
