@@ -332,14 +332,7 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
             // (the fast form compares classes already in shared memory)
             edge_words<T, FAST ? (int)CLASS_ALL : MODE, FAST>(c, row, row + lp, S1 + (int64_t)(in ? r : 0) * lp, nx,
                                                               w, W, lane, in, doY, have_next, xw, yw, zw);
-            // quads of row r: one shared-memory atomic per row segment of the warp (a warp's 32 words span at
-            // most a few rows, and same-address atomics from its lanes would be serialised)
-            {
-                const int cnt = (in && r < rows_own) ? __popc(xw) + __popc(yw) + __popc(zw) : 0;
-                const unsigned grp = __match_any_sync(kFull, live ? r : -1);
-                const int sum = (int)__reduce_add_sync(grp, (unsigned)cnt);
-                if (sum && lane == __ffs(grp) - 1) atomicAdd(&cb[r], sum);
-            }
+            if (in && r < rows_own && (xw | yw | zw)) atomicAdd(&cb[r], __popc(xw) + __popc(yw) + __popc(zw));
             if (live) {
                 PL(cur, 0, r)[w] = xw;
                 PL(cur, 1, r)[w] = yw;
@@ -371,12 +364,10 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
         if (do_cells) {
             const int prev = cur ^ 1;
             const int nrows = rows_own + extra;
-            for (int it0 = tid - lane; it0 < nrows * W; it0 += nthr) { // warp-uniform (the counts are reduced per warp)
-                const bool live = it0 + lane < nrows * W;
-                const int it = live ? it0 + lane : it0;
+            for (int it = tid; it < nrows * W; it += nthr) {
                 const int q = (int)(((uint64_t)(uint32_t)it * tl.wdiv) >> 32), w = it - q * W;
                 const int cr = q - extra; // local sample row of cy (-1 for cy = -1)
-                const bool ra = live && cr >= 0, rb = live && cr + 1 < rows_ld;
+                const bool ra = cr >= 0, rb = cr + 1 < rows_ld;
                 uint32_t v[8], p8[8];
 #pragma unroll
                 for (int d = 0; d < 2; ++d) {
@@ -410,13 +401,10 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
                 }
                 const int64_t cy = j0 + cr;
                 const int64_t rc = (cy + 1) + (ny + 1) * (cz + 1);
-                if (live) s.P[rc * g.WS + w] = pw;
-                const unsigned grp = __match_any_sync(kFull, live ? q : -1);
-                const int np_ = (int)__reduce_add_sync(grp, (unsigned)__popc(pw));
-                const int ns_ = (int)__reduce_add_sync(grp, (unsigned)deg);
-                if (np_ && lane == __ffs(grp) - 1) {
-                    atomicAdd(&cb[TY + q], np_);
-                    atomicAdd(&cb[2 * TY + 1 + q], ns_);
+                s.P[rc * g.WS + w] = pw;
+                if (pw) {
+                    atomicAdd(&cb[TY + q], __popc(pw));
+                    atomicAdd(&cb[2 * TY + 1 + q], deg);
                 }
             }
         }
