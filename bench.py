@@ -125,6 +125,11 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # let nvidia-smi finish starting up (its first query) before the timed region: its start can
+            # hold the driver for tens of milliseconds
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 10.0 and self.proc.poll() is None:
+                time.sleep(0.05)
         except OSError:
             self.proc = None
 
