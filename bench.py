@@ -720,8 +720,8 @@ def run_label_sweep(args):
 def batch_object(args, steps=None, loop=True):
     """The 256 seeded maps of uneven sizes (edges 32-256, uint8/uint16): a step is extract + 16 sweeps of every
     map.  Timed with the host clock around the whole step (host work included) after a device sync, for the
-    batched call (parallel streams, tuned tile heights), the same with the graph, and a loop of single-map
-    calls."""
+    batched call (one launch per phase, tuned tile heights), the same with the graph (one executable graph per
+    layout, updated in place), and a loop of single-map calls."""
     import torch
     import sn_synth
     from paper_2401_14906_gb300 import sn
@@ -770,8 +770,9 @@ def batch_object(args, steps=None, loop=True):
             "ms_per_step": ms_batch, "dtype": "u8/u16+f32",
             "config": {"workload": "c5_256maps_edges32-256_u8u16", "maps": len(ws), "voxels": V, "points": P,
                        "iterations": it, "timing": "host clock around each step (allocation, launches, waits)",
-                       "batched": "sn_extract_smooth_batch: counting on 8 streams, one totals wait, emission on 8 "
-                                  "streams, one sweep launch per iteration over all maps, tuned emission tiles"},
+                       "batched": "sn_extract_smooth_batch: one counting launch per label type over all maps, one "
+                                  "scan launch, one totals wait, one emission launch per label type, one sweep "
+                                  "launch per iteration over all maps, tuned emission tiles"},
             "graph_mode_ms_per_step": ms_graph, "graph_mode_gvoxels_s": V / (ms_graph / 1e3) / 1e9,
             "single_map_loop_ms_per_step": ms_loop,
             "single_map_loop_gvoxels_s": V / (ms_loop / 1e3) / 1e9 if ms_loop else None,

@@ -215,16 +215,19 @@ sn_status sn_mesh_triangles(const sn_mesh *m, const int32_t **triangles);
  * sn_extract_smooth_batch -- sn_extract (every value other than `background`
  * selected) followed by sn_smooth for each of n_maps label maps of any sizes
  * and label types.  Not in the paper: many small maps keep the GPU busy only
- * when they run side by side, so the maps' counting passes run on parallel
- * streams, one wait reads all totals back, the outputs are allocated exactly,
- * and the emission and smoothing of every map are enqueued on parallel
- * branches.
+ * when they run side by side, so each phase is one launch over all maps (per
+ * label type): the counting pass, the row scan, one wait that reads all totals
+ * back, exact allocation of the outputs, the emission, and each sweep.  A CTA
+ * finds its map in a table of per-map block offsets.  Maps whose rows are too
+ * wide for the tiles are counted and emitted map by map.
  *   labels[i]   device or host pointer, map i (nz, ny, nx) x-fastest, type types[i]
  *   dims        int64 [n_maps][3] (nx, ny, nz)
  *   spacing, origin  double [n_maps][3], or NULL for 1 and 0
  *   iterations, relaxation, constraint_distance  as for sn_smooth (box)
  *   flags       SN_BATCH_GRAPH: capture the emission and smoothing of all maps
- *               into one CUDA graph and launch it once;
+ *               into one CUDA graph and launch it once (one executable graph
+ *               is kept per layout of maps -- sizes, types, sweeps -- per host
+ *               thread, and updated in place on the next call of that layout);
  *               SN_BATCH_TUNE: choose the emission tile height per (label
  *               type, words per row, size class of rows and slices) by timing
  *               the candidates 8/16/24/32 on the first map of each class

@@ -1481,7 +1481,17 @@ sn_status sn_smooth_learned(sn_mesh *m, const sn_learner *l, int corrections, fl
 // ------------------------------------------------------------ batched maps
 namespace {
 
-constexpr int kBatchStreams = 8;
+// counting tiles of the batched call: label bytes per slot (KB) and slices per tile, at least.
+// Small maps gain from more resident tiles (16 KB slots, four per SM) and from longer ones
+// (fewer halo slices and pipeline starts); the batch itself fills the GPU.
+#ifndef SN_BATCH_SLOT_KB
+#define SN_BATCH_SLOT_KB 16
+#endif
+#ifndef SN_BATCH_MIN_KZ
+#define SN_BATCH_MIN_KZ 16
+#endif
+constexpr int kBatchSlotKB = SN_BATCH_SLOT_KB;
+constexpr int kBatchMinKz = SN_BATCH_MIN_KZ;
 
 // pinned totals of a batch, one per map; per thread, grown as needed and kept
 sn::DevTotals *batch_totals(int64_t n)
@@ -1504,27 +1514,50 @@ sn::DevTotals *batch_totals(int64_t n)
     return buf;
 }
 
-// kBatchStreams side streams and one capture-origin stream of this thread on
-// the current device (created once, kept; non-blocking, so capturable)
-cudaError_t side_streams(int dev, cudaStream_t *out)
+// the capture-origin stream of this thread on a device (created once, kept;
+// non-blocking, so capturable whatever the caller's stream is)
+cudaError_t capture_stream(int dev, cudaStream_t *out)
 {
-    thread_local std::map<int, std::vector<cudaStream_t>> cache;
-    auto &v = cache[dev];
-    if (v.empty()) {
-        for (int i = 0; i <= kBatchStreams; ++i) {
-            cudaStream_t s = nullptr;
-            cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-            if (e != cudaSuccess) {
-                for (cudaStream_t t : v) cudaStreamDestroy(t);
-                v.clear();
-                return e;
-            }
-            v.push_back(s);
+    thread_local std::map<int, cudaStream_t> cache;
+    cudaStream_t &s = cache[dev];
+    if (!s) {
+        const cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            s = nullptr;
+            return e;
         }
     }
-    for (int i = 0; i <= kBatchStreams; ++i) out[i] = v[i];
+    *out = s;
     return cudaSuccess;
 }
+
+// Host tables of the batched launches, gathered into one buffer (each table on
+// a 256-byte boundary) and copied to the device in one piece.
+struct DeviceTables {
+    std::vector<char> bytes;
+    template <typename T> size_t add(const std::vector<T> &v)
+    {
+        const size_t at = (bytes.size() + 255) / 256 * 256;
+        bytes.resize(at + sizeof(T) * v.size());
+        if (!v.empty()) std::memcpy(bytes.data() + at, v.data(), sizeof(T) * v.size());
+        return at;
+    }
+    // a copy from pageable memory: the buffer may go once the call returns
+    sn_status upload(char **out, cudaMemPool_t pool, cudaStream_t st, const char *what)
+    {
+        *out = nullptr;
+        if (bytes.empty()) bytes.resize(16);
+        sn_status r = pool_alloc((void **)out, bytes.size(), pool, st, what);
+        if (r != SN_OK) return r;
+        const cudaError_t e = cudaMemcpyAsync(*out, bytes.data(), bytes.size(), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            pool_free(*out, st);
+            *out = nullptr;
+            return cuda_fail(e, what);
+        }
+        return SN_OK;
+    }
+};
 
 // Tile height of the emission per (label type, words per row, cell rows, cell
 // slices) bucket, chosen by timing the candidates on the first map of the bucket.
@@ -1606,15 +1639,12 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    cudaStream_t side[kBatchStreams + 1];
-    if ((e = side_streams(dev, side)) != cudaSuccess) return cuda_fail(e, "side streams");
-    cudaStream_t cap = side[kBatchStreams]; // origin of the capture (the caller's stream may be the legacy one)
+    cudaStream_t cap = nullptr; // origin of the capture (the caller's stream may be the legacy one)
+    if ((e = capture_stream(dev, &cap)) != cudaSuccess) return cuda_fail(e, "capture stream");
 
     std::vector<ExtractJob> jobs((size_t)n_maps);
     sn::DevTotals *htot = nullptr;
-    std::vector<cudaEvent_t> events;
     cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
     bool capturing = false;
     auto finish = [&](sn_status r) {
         if (capturing) {
@@ -1623,10 +1653,9 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
             if (g2) cudaGraphDestroy(g2);
             cudaGetLastError();
         }
-        if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
-        if (r != SN_OK) { // work of this call may still be running on the side streams
-            for (int k = 0; k <= kBatchStreams; ++k) cudaStreamSynchronize(side[k]);
+        if (r != SN_OK) { // work of this call may still be running
+            cudaStreamSynchronize(cap);
             cudaStreamSynchronize(st);
             cudaGetLastError();
         }
@@ -1634,13 +1663,7 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
             if (r == SN_OK) j.mesh = nullptr; // handed out
             job_release(j, st);
         }
-        for (cudaEvent_t ev : events) cudaEventDestroy(ev);
         return r;
-    };
-    auto event = [&](cudaEvent_t *ev) -> cudaError_t {
-        cudaError_t e2 = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
-        if (e2 == cudaSuccess) events.push_back(*ev);
-        return e2;
     };
     const double one[3] = {1.0, 1.0, 1.0}, zero[3] = {0.0, 0.0, 0.0};
 
@@ -1690,21 +1713,92 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
         jobs[i].dtot = dtot_all + i;
     }
 
-    // 2. Passes 1-3 and the scans of all maps on the side streams, then one wait
-    cudaEvent_t fork = nullptr;
-    if ((e = event(&fork)) != cudaSuccess || (e = cudaEventRecord(fork, st)) != cudaSuccess)
-        return finish(cuda_fail(e, "batch fork"));
-    for (int k = 0; k < kBatchStreams; ++k)
-        if ((e = cudaStreamWaitEvent(side[k], fork, 0)) != cudaSuccess) return finish(cuda_fail(e, "batch fork"));
-    for (int64_t i = 0; i < n_maps; ++i) {
-        sn_status r = job_count(jobs[i], side[i % kBatchStreams], true);
+    // 2. Passes 1-3 and the row scans of all maps: one counting launch per label type and row
+    //    alignment over the maps whose rows fit a counting tile (the two-kernel form for the
+    //    rest, map by map), one scan launch over all maps, then one wait
+    {
+        struct CountGroup {
+            std::vector<sn::CountBatchMap> maps;
+            std::vector<uint32_t> start;
+            uint64_t blocks = 0;
+            size_t smem = 0;
+        } groups[3][2];
+        std::vector<int64_t> two_kernel;
+        std::vector<sn::ScanBatchMap> scans((size_t)n_maps);
+        std::vector<uint32_t> scan_start((size_t)n_maps);
+        uint64_t scan_blocks = 0;
+        for (int64_t i = 0; i < n_maps; ++i) {
+            ExtractJob &j = jobs[i];
+            sn::CountTiling tl;
+            size_t smem = 0;
+            const int ti = j.type == SN_U8 ? 0 : j.type == SN_U16 ? 1 : 2;
+            bool batched = j.cls.mode == sn::CLASS_ALL &&
+                           sn::count_tiling(j.type, j.dlabels, j.g, &tl, &smem, kBatchSlotKB, kBatchMinKz);
+            if (batched) {
+                CountGroup &G = groups[ti][tl.aligned ? 1 : 0];
+                sn::CountBatchMap d;
+                std::memset(&d, 0, sizeof(d));
+                d.lab = j.dlabels;
+                d.c = j.cls;
+                d.g = j.g;
+                d.s = j.s;
+                d.tl = tl;
+                d.tot = j.dtot;
+                d.gx = (j.g.ny + tl.ty - 1) / tl.ty;
+                const uint64_t nb = (uint64_t)d.gx * (uint64_t)(tl.zt1 - tl.zt0);
+                batched = G.blocks + nb <= 0x7fffffffull;
+                if (batched) {
+                    G.start.push_back((uint32_t)G.blocks);
+                    G.blocks += nb;
+                    G.maps.push_back(d);
+                    G.smem = std::max(G.smem, smem);
+                }
+            }
+            if (!batched) two_kernel.push_back(i);
+            sn::ScanBatchMap &sc = scans[i];
+            std::memset(&sc, 0, sizeof(sc));
+            sc.g = j.g;
+            sc.s = j.s;
+            sc.tot = j.dtot;
+            sc.ntiles = (j.g.Rc + sn::kScanTile - 1) / sn::kScanTile;
+            scan_start[i] = (uint32_t)scan_blocks;
+            scan_blocks += (uint64_t)sc.ntiles;
+        }
+        if (scan_blocks > 0x7fffffffull) return finish(fail(SN_EINVAL, "too many cell rows in one batch"));
+        // the tables in one device block (one copy from pageable memory: the vectors may go once it returns)
+        DeviceTables tabs;
+        size_t at_count[3][2][2] = {}, at_scan = tabs.add(scans), at_scan_start = tabs.add(scan_start);
+        for (int ti = 0; ti < 3; ++ti)
+            for (int f = 0; f < 2; ++f)
+                if (!groups[ti][f].maps.empty()) {
+                    at_count[ti][f][0] = tabs.add(groups[ti][f].maps);
+                    at_count[ti][f][1] = tabs.add(groups[ti][f].start);
+                }
+        char *dt = nullptr;
+        sn_status r = tabs.upload(&dt, jobs[0].pool, st, "batch counting tables");
         if (r != SN_OK) return finish(r);
-    }
-    for (int k = 0; k < kBatchStreams; ++k) {
-        cudaEvent_t join = nullptr;
-        if ((e = event(&join)) != cudaSuccess || (e = cudaEventRecord(join, side[k])) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess)
-            return finish(cuda_fail(e, "batch join"));
+        jobs[0].temps.push_back(dt);
+        static const sn_label_type kTypes[3] = {SN_U8, SN_U16, SN_U32};
+        for (int ti = 0; ti < 3; ++ti)
+            for (int f = 0; f < 2; ++f) {
+                const CountGroup &G = groups[ti][f];
+                if (G.maps.empty()) continue;
+                e = sn::launch_count_batch(kTypes[ti], f == 1,
+                                           reinterpret_cast<const sn::CountBatchMap *>(dt + at_count[ti][f][0]),
+                                           reinterpret_cast<const uint32_t *>(dt + at_count[ti][f][1]),
+                                           (int)G.maps.size(), (uint32_t)G.blocks, G.smem, st);
+                if (e != cudaSuccess) return finish(cuda_fail(e, "batched counting launch"));
+            }
+        for (int64_t i : two_kernel) {
+            ExtractJob &j = jobs[i];
+            if ((e = sn::launch_planes(j.type, j.dlabels, j.cls, j.g, j.s, st)) != cudaSuccess ||
+                (e = sn::launch_cellrows(j.g, j.s, st)) != cudaSuccess)
+                return finish(cuda_fail(e, "counting launch"));
+        }
+        e = sn::launch_scan_batch(reinterpret_cast<const sn::ScanBatchMap *>(dt + at_scan),
+                                  reinterpret_cast<const uint32_t *>(dt + at_scan_start), (int)n_maps,
+                                  (uint32_t)scan_blocks, st);
+        if (e != cudaSuccess) return finish(cuda_fail(e, "batched scan launch"));
     }
     e = cudaMemcpyAsync(htot, dtot_all, sizeof(sn::DevTotals) * (size_t)n_maps, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1721,10 +1815,12 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
         }
     }
 
-    // the table-driven prologue (cell-centre tables, meta words) and epilogue
-    // (last stencil offsets) of all meshes
-    sn::BatchMeshPrep *prep = nullptr;
+    // the tables of the launches below, uploaded in one piece: the prologue (cell-centre
+    // tables, meta words) and epilogue (last stencil offsets) of all meshes, the batched
+    // emission (maps whose rows fit an emission tile, per label type) and the sweeps
+    DeviceTables tabs;
     int64_t prep_entries = 0;
+    size_t at_prep = 0;
     {
         std::vector<sn::BatchMeshPrep> tab((size_t)n_maps);
         for (int64_t i = 0; i < n_maps; ++i) {
@@ -1744,22 +1840,57 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
             }
             prep_entries += j.dims[0] + j.dims[1] + j.dims[2] + 3;
         }
-        sn_status r = pool_alloc((void **)&prep, sizeof(sn::BatchMeshPrep) * (size_t)n_maps, jobs[0].pool, st,
-                                 "batch prologue table");
-        if (r != SN_OK) return finish(r);
-        jobs[0].temps.push_back(prep);
-        // (a copy from pageable memory: the host vector may go once the call returns)
-        e = cudaMemcpyAsync(prep, tab.data(), sizeof(sn::BatchMeshPrep) * (size_t)n_maps, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return finish(cuda_fail(e, "batch prologue table"));
+        at_prep = tabs.add(tab);
     }
-
-    // the sweep table of all meshes (device copy, freed with the scratch)
-    sn::SmoothBatchMap *smooth_table = nullptr;
-    uint32_t *smooth_table_blocks = nullptr;
+    struct EmitGroup {
+        std::vector<sn::EmitBatchMap> maps;
+        std::vector<uint32_t> start;
+        uint64_t blocks = 0;
+        size_t smem = 0;
+        size_t at_maps = 0, at_start = 0;
+    } egroups[3];
+    std::vector<int64_t> emit_single;
+    for (int64_t i = 0; i < n_maps; ++i) {
+        const ExtractJob &j = jobs[i];
+        const sn_mesh *m = j.mesh;
+        sn::TileGeom tg;
+        size_t smem = 0;
+        const int ti = j.type == SN_U8 ? 0 : j.type == SN_U16 ? 1 : 2;
+        bool batched = j.cls.mode == sn::CLASS_ALL && sn::emit_tiling(j.g, rows[i], m->np + m->nq, &tg, &smem) &&
+                       smem + 32 + sizeof(sn::EmitBatchMap) <= 227 * 1024;
+        if (batched) {
+            EmitGroup &G = egroups[ti];
+            sn::EmitBatchMap d;
+            std::memset(&d, 0, sizeof(d));
+            d.lab = j.dlabels;
+            d.c = j.cls;
+            d.g = j.g;
+            d.s = j.s;
+            d.m = m->a;
+            d.tot = j.dtot;
+            d.tg = tg;
+            d.gx = (j.g.ny + 1 + tg.ty - 1) / tg.ty;
+            const uint64_t nb = (uint64_t)d.gx * (uint64_t)(j.g.nz + 1);
+            batched = G.blocks + nb <= 0x7fffffffull;
+            if (batched) {
+                G.start.push_back((uint32_t)G.blocks);
+                G.blocks += nb;
+                G.maps.push_back(d);
+                G.smem = std::max(G.smem, smem);
+            }
+        }
+        if (!batched) emit_single.push_back(i);
+    }
+    for (auto &G : egroups)
+        if (!G.maps.empty()) {
+            G.at_maps = tabs.add(G.maps);
+            G.at_start = tabs.add(G.start);
+        }
     uint32_t total_blocks = 0;
     bool fusable = true; // sweeps 1 and 2 in one launch: every mesh has neighbour records
     for (int64_t i = 0; i < n_maps; ++i) fusable = fusable && jobs[i].mesh->a.rec != sn::REC_CSR;
     const int launches = sn::sweep_launches(iterations, fusable);
+    size_t at_sweep = 0, at_sweep_start = 0;
     if (iterations > 0) {
         std::vector<sn::SmoothBatchMap> tab((size_t)n_maps);
         std::vector<uint32_t> starts((size_t)n_maps);
@@ -1782,21 +1913,19 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
         }
         if (nb > 0x7fffffffull) return finish(fail(SN_EINVAL, "too many points in one batch"));
         total_blocks = (uint32_t)nb;
-        const size_t tb = sizeof(sn::SmoothBatchMap) * (size_t)n_maps, sb = sizeof(uint32_t) * (size_t)n_maps;
-        char *d = nullptr;
-        sn_status r = pool_alloc((void **)&d, tb + 256 + sb, jobs[0].pool, st, "sweep table");
-        if (r != SN_OK) return finish(r);
-        jobs[0].temps.push_back(d);
-        smooth_table = reinterpret_cast<sn::SmoothBatchMap *>(d);
-        smooth_table_blocks = reinterpret_cast<uint32_t *>(d + (tb + 255) / 256 * 256);
-        e = cudaMemcpyAsync(smooth_table, tab.data(), tb, cudaMemcpyHostToDevice, st);
-        // (copies from pageable memory: the host vectors may go once the calls return)
-        if (e == cudaSuccess) e = cudaMemcpyAsync(smooth_table_blocks, starts.data(), sb, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return finish(cuda_fail(e, "sweep table"));
+        at_sweep = tabs.add(tab);
+        at_sweep_start = tabs.add(starts);
     }
+    char *dt = nullptr;
+    {
+        sn_status r = tabs.upload(&dt, jobs[0].pool, st, "batch tables");
+        if (r != SN_OK) return finish(r);
+        jobs[0].temps.push_back(dt);
+    }
+    const sn::BatchMeshPrep *prep = reinterpret_cast<const sn::BatchMeshPrep *>(dt + at_prep);
 
-    // 4. Pass 4 and the smoothing of every map on the side streams, captured
-    //    into one graph (maps on parallel branches, launched once on the
+    // 4. Pass 4 and the smoothing of every map: one emission launch per label type, then one
+    //    launch per sweep over all meshes, captured into one graph (launched once on the
     //    caller's stream) or launched directly
     const bool use_graph = (flags & SN_BATCH_GRAPH) != 0;
     cudaStream_t origin_st = use_graph ? cap : st;
@@ -1807,36 +1936,62 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
     }
     if ((e = sn::launch_prologue_batch(prep, (int)n_maps, prep_entries, origin_st)) != cudaSuccess)
         return finish(cuda_fail(e, "batch prologue"));
-    cudaEvent_t fork2 = nullptr;
-    if ((e = event(&fork2)) != cudaSuccess || (e = cudaEventRecord(fork2, origin_st)) != cudaSuccess)
-        return finish(cuda_fail(e, "batch fork"));
-    for (int k = 0; k < kBatchStreams; ++k)
-        if ((e = cudaStreamWaitEvent(side[k], fork2, 0)) != cudaSuccess) return finish(cuda_fail(e, "batch fork"));
     const float half = 0.5f * constraint_distance;
-    for (int64_t i = 0; i < n_maps; ++i) {
-        sn_status r = job_emit(jobs[i], side[i % kBatchStreams], rows[i], true);
-        if (r != SN_OK) return finish(r);
+    static const sn_label_type kEmitTypes[3] = {SN_U8, SN_U16, SN_U32};
+    for (int ti = 0; ti < 3; ++ti) {
+        const EmitGroup &G = egroups[ti];
+        if (G.maps.empty()) continue;
+        e = sn::launch_emit_tile_batch(kEmitTypes[ti], reinterpret_cast<const sn::EmitBatchMap *>(dt + G.at_maps),
+                                       reinterpret_cast<const uint32_t *>(dt + G.at_start), (int)G.maps.size(),
+                                       (uint32_t)G.blocks, G.smem, origin_st);
+        if (e != cudaSuccess) return finish(cuda_fail(e, "batched emission launch"));
     }
-    for (int k = 0; k < kBatchStreams; ++k) {
-        cudaEvent_t join = nullptr;
-        if ((e = event(&join)) != cudaSuccess || (e = cudaEventRecord(join, side[k])) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(origin_st, join, 0)) != cudaSuccess)
-            return finish(cuda_fail(e, "batch join"));
+    for (int64_t i : emit_single) {
+        sn_status r = job_emit(jobs[i], origin_st, rows[i], true);
+        if (r != SN_OK) return finish(r);
     }
     if ((e = sn::launch_epilogue_batch(prep, (int)n_maps, origin_st)) != cudaSuccess)
         return finish(cuda_fail(e, "batch epilogue"));
     // the sweeps of all meshes: one launch per sweep
-    if (iterations > 0 && smooth_table) {
-        e = sn::launch_smooth_batch(smooth_table, smooth_table_blocks, (int)n_maps, total_blocks, iterations,
-                                    fusable, relaxation, half, 0, origin_st);
+    if (iterations > 0 && total_blocks > 0) {
+        e = sn::launch_smooth_batch(reinterpret_cast<const sn::SmoothBatchMap *>(dt + at_sweep),
+                                    reinterpret_cast<const uint32_t *>(dt + at_sweep_start), (int)n_maps,
+                                    total_blocks, iterations, fusable, relaxation, half, 0, origin_st);
         if (e != cudaSuccess) return finish(cuda_fail(e, "smoothing launch"));
     }
     if (use_graph) {
         capturing = false;
         if ((e = cudaStreamEndCapture(cap, &graph)) != cudaSuccess) return finish(cuda_fail(e, "graph capture end"));
-        if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
+        // one executable graph per batch layout (device, maps' sizes and types, sweeps, flags), kept and
+        // updated in place with the new call's arguments: an update costs far less than an instantiation
+        uint64_t key = mix64((uint64_t)dev) ^ mix64(0x5b17ull + (uint64_t)n_maps);
+        key = mix64(key ^ (uint64_t)iterations) ^ mix64(key + (uint64_t)flags + (fusable ? 77u : 0u));
+        for (int64_t i = 0; i < n_maps; ++i)
+            key = mix64(key ^ (uint64_t)jobs[i].dims[0] ^ ((uint64_t)jobs[i].dims[1] << 21) ^
+                        ((uint64_t)jobs[i].dims[2] << 42) ^ ((uint64_t)jobs[i].type << 62) ^ (uint64_t)rows[i]);
+        thread_local std::map<uint64_t, cudaGraphExec_t> cache;
+        if (cache.size() >= 32 && !cache.count(key)) { // bounded: many layouts start it over
+            for (auto &kv : cache)
+                if (kv.second) cudaGraphExecDestroy(kv.second);
+            cache.clear();
+        }
+        cudaGraphExec_t &cached = cache[key];
+        bool updated = false;
+        if (cached) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(cached, graph, &info) == cudaSuccess) {
+                updated = true;
+            } else {
+                cudaGetLastError();
+                cudaGraphExecDestroy(cached);
+                cached = nullptr;
+            }
+        }
+        if (!updated && (e = cudaGraphInstantiate(&cached, graph, 0)) != cudaSuccess) {
+            cached = nullptr;
             return finish(cuda_fail(e, "graph instantiate"));
-        if ((e = cudaGraphLaunch(exec, st)) != cudaSuccess) return finish(cuda_fail(e, "graph launch"));
+        }
+        if ((e = cudaGraphLaunch(cached, st)) != cudaSuccess) return finish(cuda_fail(e, "graph launch"));
     }
     for (int64_t i = 0; i < n_maps; ++i) {
         jobs[i].mesh->stream = st;

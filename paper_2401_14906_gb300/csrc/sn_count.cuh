@@ -1,6 +1,6 @@
 // sn_count.cuh -- Passes 1-3 of the extraction as one streaming tile (Sec. 2.2-2.3,
-// 3.1-3.4); the body of k_count (sn_extract.cu), which the batched extraction
-// also launches, once per map.
+// 3.1-3.4); the body of k_count (sn_extract.cu) and of k_count_batch
+// (sn_batch.cu), which runs it for the tiles of many maps in one launch.
 #pragma once
 
 #include "sn_device.cuh"
@@ -232,6 +232,7 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
         return planes + (size_t)buf * plane_words + (p * (TY + 1) + r) * W;
     };
 
+    const int64_t sp = tl.spitch; // elements between rows in a slot
     const uint32_t slice_bytes = (uint32_t)(rows_ld * lp * (int64_t)sizeof(T));
     auto issue = [&](int64_t kk) {
         if (kk >= k_ld_end) return;
@@ -240,9 +241,15 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
         T *dst = reinterpret_cast<T *>(slots + (size_t)slot * tl.slot_bytes);
         if (tl.aligned) {
             if (tid == 0) {
+                // realign: the 16-byte aligned span around the slice block, to the staging area
+                const uintptr_t a = reinterpret_cast<uintptr_t>(src);
+                const uintptr_t a0 = tl.realign ? a & ~(uintptr_t)15 : a;
+                const uint32_t bytes = tl.realign ? (uint32_t)(((a + slice_bytes + 15) & ~(uintptr_t)15) - a0)
+                                                  : slice_bytes;
+                void *to = tl.realign ? (void *)(slots + (size_t)slot * tl.slot_bytes + tl.stage_off) : (void *)dst;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&bars[slot], slice_bytes);
-                bulk_load(dst, src, slice_bytes, &bars[slot]);
+                mbar_expect_tx(&bars[slot], bytes);
+                bulk_load(to, reinterpret_cast<const void *>(a0), bytes, &bars[slot]);
                 // and bring the slice kCountPrefetch further on into L2, so that its copy,
                 // issued kCountPrefetch steps later, is served from L2
                 if (kCountPrefetch && kk + kCountPrefetch < k_ld_end)
@@ -253,6 +260,22 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
         } else {
             const int64_t n = (int64_t)rows_ld * lp;
             for (int64_t e = tid; e < n; e += nthr) dst[e] = src[e];
+        }
+    };
+
+    // realign: move the rows of slice kq from the staging area to the slot at a 16-byte pitch,
+    // one 4-byte word per thread and step (two staged words and a funnel shift)
+    auto realign_slice = [&](int64_t kq) {
+        uint8_t *base = slots + (size_t)((kq - k0) % kCountSlots) * tl.slot_bytes;
+        const uint32_t *stg = reinterpret_cast<const uint32_t *>(base + tl.stage_off);
+        uint32_t *out = reinterpret_cast<uint32_t *>(base);
+        const uint32_t o0 = (uint32_t)(reinterpret_cast<uintptr_t>(lab + (kq * ny + j0) * lp) & 15);
+        const int rb = (int)(lp * (int64_t)sizeof(T)), rw = (rb + 3) >> 2;
+        const int pw = (int)(sp * (int64_t)sizeof(T)) >> 2;
+        for (int e = tid; e < rows_ld * rw; e += nthr) {
+            const int r = e / rw, j = e - r * rw;
+            const uint32_t S = o0 + (uint32_t)(r * rb) + 4u * (uint32_t)j;
+            out[r * pw + j] = __funnelshift_r(stg[S >> 2], stg[(S >> 2) + 1], 8u * (S & 3u));
         }
     };
 
@@ -299,6 +322,11 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
                 }
             }
         }
+        if (tl.realign) {
+            __syncthreads(); // thread 0 has seen the staged slices land
+            if (kk == k0 && have) realign_slice(kk);
+            if (have_next) realign_slice(kk + 1);
+        }
         // (the previous reads of this set ended before the previous step's second barrier)
         for (int e = tid; e < cstride; e += nthr) cb[e] = 0;
         T *S0w = reinterpret_cast<T *>(slots + (size_t)((kk - k0) % kCountSlots) * tl.slot_bytes);
@@ -309,7 +337,7 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
             // packed compares below compare classes; slice kk arrived as slice kk+1
             // of the previous step unless this is the first step
             __syncthreads();
-            const int64_t n = (int64_t)rows_ld * lp;
+            const int64_t n = (int64_t)rows_ld * sp;
             if (kk == k0 && have)
                 for (int64_t e = tid; e < n; e += nthr) S0w[e] = (T)kappa<MODE>(c, (uint32_t)S0w[e]);
             if (have_next)
@@ -326,11 +354,11 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
             const bool live = it < (TY + 1) * W;
             const int r = (int)(((uint64_t)(uint32_t)it * tl.wdiv) >> 32), w = it - r * W;
             const bool in = live && have && r < rows_ld;
-            const T *row = S0 + (int64_t)(in ? r : 0) * lp;
+            const T *row = S0 + (int64_t)(in ? r : 0) * sp;
             const bool doY = r < rows_own && r + 1 < rows_ld;
             uint32_t xw, yw, zw;
             // (the fast form compares classes already in shared memory)
-            edge_words<T, FAST ? (int)CLASS_ALL : MODE, FAST>(c, row, row + lp, S1 + (int64_t)(in ? r : 0) * lp, nx,
+            edge_words<T, FAST ? (int)CLASS_ALL : MODE, FAST>(c, row, row + sp, S1 + (int64_t)(in ? r : 0) * sp, nx,
                                                               w, W, lane, in, doY, have_next, xw, yw, zw);
             if (in && r < rows_own && (xw | yw | zw)) atomicAdd(&cb[r], __popc(xw) + __popc(yw) + __popc(zw));
             if (live) {

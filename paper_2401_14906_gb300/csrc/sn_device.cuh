@@ -195,5 +195,40 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                  : "memory");
 }
 
+// Batched launches over many maps: the map i with start[i] <= b < start[i + 1]
+// (start ascending from 0; the last map runs to the grid's end), found by the
+// whole CTA and returned to every thread.  Up to four entries per thread are
+// tested in one round of independent loads; larger tables take one thread's
+// binary search.  *sh is a shared-memory word of the caller.
+__device__ __forceinline__ int find_map_cta(const uint32_t *__restrict__ start, int n, uint32_t b, int *sh)
+{
+    if (n <= 4 * (int)blockDim.x) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t s1 = i + 1 < n ? start[i + 1] : 0xffffffffu;
+            if (start[i] <= b && b < s1) *sh = i;
+        }
+    } else if (threadIdx.x == 0) {
+        int lo = 0;
+        for (int hi = n; hi - lo > 1;) {
+            const int mid = (lo + hi) >> 1;
+            if (start[mid] <= b) lo = mid;
+            else hi = mid;
+        }
+        *sh = lo;
+    }
+    __syncthreads();
+    return *sh;
+}
+
+// copy one descriptor into shared memory with the whole CTA (then a barrier)
+template <typename D> __device__ __forceinline__ void load_map(D *dst, const D *__restrict__ src)
+{
+    static_assert(sizeof(D) % 8 == 0, "descriptors are copied in 8-byte words");
+    const uint64_t *s = reinterpret_cast<const uint64_t *>(src);
+    uint64_t *d = reinterpret_cast<uint64_t *>(dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(D) / 8); k += blockDim.x) d[k] = s[k];
+    __syncthreads();
+}
+
 } // namespace dev
 } // namespace sn

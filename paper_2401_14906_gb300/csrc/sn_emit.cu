@@ -82,12 +82,9 @@ int default_rows(int W, int WS, int lcap)
 
 } // namespace
 
-cudaError_t launch_emit_tile(int type, const void *labels, const Classifier &c, const Geometry &g,
-                             const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st, int rows,
-                             int64_t items)
+bool emit_tiling(const Geometry &g, int rows, int64_t items, TileGeom *out, size_t *smem)
 {
-    if (g.W > kTileMaxW || g.nz + 1 > 65535) return cudaErrorNotSupported;
-    if (rows < 0 || rows > kEmitMaxRows) return cudaErrorInvalidValue;
+    if (g.W > kTileMaxW || g.nz + 1 > 65535) return false;
     TileGeom tg;
     // position list: chunks of about a 20-row tile's points or quads, 1024 to 4096 entries
     const double per_row = (double)items / (double)((g.ny + 1) * (g.nz + 1));
@@ -97,7 +94,19 @@ cudaError_t launch_emit_tile(int type, const void *labels, const Classifier &c, 
     tg.WS = (int)g.WS;
     tg.ns = 3 * (tg.ty + 2);
     tg.wdiv = (0x100000000ull + (uint64_t)g.W - 1) / (uint64_t)g.W;
-    const size_t smem = sizeof(uint32_t) * (size_t)TileSmem(tg.ty, tg.W, tg.WS, tg.lcap).total;
+    *out = tg;
+    *smem = sizeof(uint32_t) * (size_t)TileSmem(tg.ty, tg.W, tg.WS, tg.lcap).total;
+    return true;
+}
+
+cudaError_t launch_emit_tile(int type, const void *labels, const Classifier &c, const Geometry &g,
+                             const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st, int rows,
+                             int64_t items)
+{
+    if (rows < 0 || rows > kEmitMaxRows) return cudaErrorInvalidValue;
+    TileGeom tg;
+    size_t smem = 0;
+    if (!emit_tiling(g, rows, items, &tg, &smem)) return cudaErrorNotSupported;
     ProfScope ps("k_emit_tile", st);
     if (c.mode == CLASS_ALL) return emit_tile_m<CLASS_ALL>(type, labels, c, g, s, m, tot, tg, smem, st);
     if (c.mode == CLASS_BITMAP) return emit_tile_m<CLASS_BITMAP>(type, labels, c, g, s, m, tot, tg, smem, st);

@@ -1,6 +1,6 @@
 // sn_emit_tile.cuh -- Pass 4 of the extraction (Sec. 2.3 "Generate output", Sec.
-// 3.6) over a tile of cell rows; the body of k_emit_tile (sn_emit.cu), which the
-// batched extraction also launches, once per map.
+// 3.6) over a tile of cell rows; the body of k_emit_tile (sn_emit.cu) and of
+// k_emit_tile_batch (sn_batch.cu), which runs it for the tiles of many maps.
 #pragma once
 
 #include "sn_device.cuh"

@@ -539,37 +539,61 @@ cudaError_t launch_epilogue_batch(const BatchMeshPrep *maps, int n, cudaStream_t
     return cudaGetLastError();
 }
 
-bool count_tiling(int type, const void *labels, const Geometry &g, CountTiling *out, size_t *smem_out)
+bool count_tiling(int type, const void *labels, const Geometry &g, CountTiling *out, size_t *smem_out, int slot_kb,
+                  int min_kz)
 {
     const int64_t row_bytes = g.lp * (int64_t)type; // label rows are g.lp elements apart
 #ifndef SN_COUNT_SLOT_KB
 #define SN_COUNT_SLOT_KB 32
 #endif
-    constexpr int64_t kSlotBudget = SN_COUNT_SLOT_KB * 1024; // bytes of labels per slot
+    const int64_t kSlotBudget = (slot_kb > 0 ? slot_kb : SN_COUNT_SLOT_KB) * 1024; // bytes of labels per slot
+    // Three forms: rows on 16-byte boundaries arrive by bulk copies as they are
+    // (direct); other rows arrive as the 16-byte aligned span around the slice
+    // block in a staging area and are moved to a 16-byte pitch (realign); rows
+    // too long for that are copied element by element and compared one sample
+    // at a time (scalar).
+    const bool direct = (row_bytes % 16 == 0) && ((reinterpret_cast<uintptr_t>(labels) & 15) == 0);
+    const int64_t pitch_bytes = (row_bytes + 15) / 16 * 16;
+    // staging: the span (at most rows * row_bytes + 30 bytes, a multiple of 16) and the word read past it
+    auto stage_bytes = [&](int t) -> int64_t { return ((t + 1) * row_bytes + 15 + 15) / 16 * 16 + 16; };
+    auto aligned_rows = [&](int t) -> int64_t { return ((t + 1) * pitch_bytes + 127) / 128 * 128; };
+    auto slot_size = [&](int form, int t) -> int64_t {
+        return form == 1 ? aligned_rows(t) + stage_bytes(t) : (t + 1) * row_bytes;
+    };
     // rows per tile: fit the slot budget, and make the (rows + 1) * W edge-word
     // items of a slice fill the 256 threads as evenly as possible
-    int ty = 0;
-    double best = -1.0;
-    for (int t = 1; t <= kCountMaxTY; ++t) {
-        if ((t + 1) * row_bytes > kSlotBudget) break;
-        const int64_t items = (int64_t)(t + 1) * g.W;
-        const double fill = (double)(t * g.W) / (double)(((items + kCountThreads - 1) / kCountThreads) * kCountThreads);
-        if (fill > best + 1e-9) {
-            best = fill;
-            ty = t;
+    auto rows_for = [&](int form) {
+        int ty = 0;
+        double best = -1.0;
+        for (int t = 1; t <= kCountMaxTY; ++t) {
+            if (slot_size(form, t) > kSlotBudget) break;
+            const int64_t items = (int64_t)(t + 1) * g.W;
+            const double fill =
+                (double)(t * g.W) / (double)(((items + kCountThreads - 1) / kCountThreads) * kCountThreads);
+            if (fill > best + 1e-9) {
+                best = fill;
+                ty = t;
+            }
         }
-    }
+        return ty;
+    };
+    int form = direct ? 0 : 1; // 0 direct, 1 realign, 2 scalar
+    int ty = rows_for(form);
+    if (ty == 0 && form == 1) ty = rows_for(form = 2);
     if (ty == 0 || g.W > 4096) return false;
     CountTiling tl;
     tl.ty = ty;
     tl.W = (int)g.W;
     tl.wdiv = (0x100000000ull + (uint64_t)g.W - 1) / (uint64_t)g.W;
-    tl.slot_bytes = (int)((((ty + 1) * row_bytes) + 127) / 128 * 128);
-    tl.aligned = (row_bytes % 16 == 0) && ((reinterpret_cast<uintptr_t>(labels) & 15) == 0);
-    // enough z-tiles to fill the GPU about twice over, slices per tile in [4, 64]
+    tl.slot_bytes = (int)((slot_size(form, ty) + 127) / 128 * 128);
+    tl.aligned = form != 2;
+    tl.realign = form == 1;
+    tl.stage_off = form == 1 ? (int)aligned_rows(ty) : 0;
+    tl.spitch = form == 1 ? pitch_bytes / type : g.lp;
+    // enough z-tiles to fill the GPU about twice over, slices per tile in [min_kz, 64]
     const int64_t ytiles = (g.ny + ty - 1) / ty;
     int64_t kz = (g.nz * ytiles + 2 * 152 * 4 - 1) / (2 * 152 * 4);
-    if (kz < 4) kz = 4;
+    if (kz < min_kz) kz = min_kz;
     if (kz > 64) kz = 64;
     tl.kz = (int)kz;
     tl.zt0 = 0;

@@ -113,7 +113,12 @@ struct CountTiling {
     int W;
     uint64_t wdiv;    // ceil(2^32 / W): it / W == (it * wdiv) >> 32 while it * W < 2^32
     int slot_bytes;   // bytes of one label slot, rounded up to 128
-    int aligned;      // rows start on 16-byte boundaries: bulk copies allowed
+    int aligned;      // slices arrive by bulk copies and are compared as packed 16-byte chunks
+    int realign;      // rows are not on 16-byte boundaries: a bulk copy brings the 16-byte aligned
+                      // span around the slice block to the slot's staging area at stage_off, and the
+                      // tile moves the rows into the slot at a pitch of spitch elements (16-byte multiple)
+    int stage_off;    // bytes from a slot's start to its staging area (realign only)
+    int64_t spitch;   // elements between rows in a slot (lp unless realign)
     int64_t zt0, zt1; // the launch covers z-tiles [zt0, zt1) (tile z covers slices [z*kz, z*kz + kz], the last one a halo)
 };
 
@@ -161,7 +166,10 @@ cudaError_t launch_count(int type, const void *labels, const Classifier &c, cons
 // The same pass in pieces: the tiling launch_count would use (false: not
 // supported, the two-kernel form is used then), the clearing of the quad counts
 // it starts with, and a launch over z-tiles [zt0, zt1) only.
-bool count_tiling(int type, const void *labels, const Geometry &g, CountTiling *tl, size_t *smem);
+// slot_kb: the bytes of labels a slot may hold, in KB (0: the default); min_kz: slices per
+// tile at least (tiles are made longer than that only to fill the GPU twice over).
+bool count_tiling(int type, const void *labels, const Geometry &g, CountTiling *tl, size_t *smem, int slot_kb = 0,
+                  int min_kz = 4);
 cudaError_t launch_count_clear(const Geometry &g, const ExtractScratch &s, cudaStream_t st);
 cudaError_t launch_count_range(int type, const void *labels, const Classifier &c, const Geometry &g,
                                const ExtractScratch &s, DevTotals *tot, CountTiling tl, size_t smem, int64_t zt0,
@@ -181,6 +189,49 @@ cudaError_t launch_emit(int type, const void *labels, const Classifier &c, const
 cudaError_t launch_emit_tile(int type, const void *labels, const Classifier &c, const Geometry &g,
                              const ExtractScratch &s, const MeshArrays &m, DevTotals *tot, cudaStream_t st,
                              int rows = 0, int64_t items = 0);
+
+// Passes 1-4 of many maps, one launch per phase and label type (sn_batch.cu).
+// Each table entry describes one map (built on the host, copied to the
+// device); CTA b works on block b - block_start[i] of the map i with
+// block_start[i] <= b < block_start[i+1].  The maps use the default classifier
+// (every non-background label) and, for counting and emission, tiles that fit
+// shared memory; a map's tile shape is its own, the launch's shared memory the
+// largest of them.
+struct CountBatchMap {
+    const void *lab;
+    Classifier c;
+    Geometry g;
+    ExtractScratch s;
+    CountTiling tl;
+    DevTotals *tot;
+    int64_t gx; // row tiles of a slice block (the single-map grid's x extent)
+};
+struct ScanBatchMap {
+    Geometry g;
+    ExtractScratch s;
+    DevTotals *tot;
+    int64_t ntiles;
+};
+struct EmitBatchMap {
+    const void *lab;
+    Classifier c;
+    Geometry g;
+    ExtractScratch s;
+    MeshArrays m;
+    DevTotals *tot;
+    TileGeom tg;
+    int64_t gx; // tiles of a slice (the single-map grid's x extent)
+};
+// fast: every map's rows start on 16-byte boundaries (CountTiling::aligned)
+cudaError_t launch_count_batch(int type, bool fast, const CountBatchMap *maps, const uint32_t *block_start, int n,
+                               uint32_t blocks, size_t tile_smem, cudaStream_t st);
+cudaError_t launch_scan_batch(const ScanBatchMap *maps, const uint32_t *block_start, int n, uint32_t blocks,
+                              cudaStream_t st);
+cudaError_t launch_emit_tile_batch(int type, const EmitBatchMap *maps, const uint32_t *block_start, int n,
+                                   uint32_t blocks, size_t tile_smem, cudaStream_t st);
+// the emission tiling launch_emit_tile uses for these arguments (false: rows too
+// wide for the tiles); *smem = its dynamic shared memory
+bool emit_tiling(const Geometry &g, int rows, int64_t items, TileGeom *tg, size_t *smem);
 
 // Many meshes' cell-centre tables and meta words in one launch, and their last
 // stencil offsets (sten_tail = *sten_total) in another (sn_extract.cu).

@@ -31,51 +31,59 @@ __global__ void __launch_bounds__(256) k_centres(MeshArrays m, int64_t np)
 
 // Launch t of the sweeps of many meshes: CTA b works on block b - block_start[i]
 // of the mesh i with block_start[i] <= b < block_start[i+1].  `fused`: launch 0
-// runs sweeps 1 and 2.
+// runs sweeps 1 and 2.  The CTA finds its mesh and copies the mesh's table
+// entry with one round of loads; the sweep arguments then sit in shared memory
+// (thread 0 writes them), where the sweep reads each as it needs it instead of
+// holding all of them in registers: the kernel keeps the single-mesh sweep's
+// full residency.
 template <bool FUSED>
-__global__ void __launch_bounds__(kSweepThreads) k_smooth_batch(const SmoothBatchMap *maps,
-                                                                const uint32_t *block_start, int n, int t,
-                                                                int launches, float lam, float h, int sphere)
+__global__ void __launch_bounds__(kSweepThreads, 2048 / kSweepThreads)
+    k_smooth_batch(const SmoothBatchMap *maps, const uint32_t *block_start, int n, int t, int launches, float lam,
+                   float h, int sphere)
 {
+    __shared__ __align__(16) uint64_t args_sh[(sizeof(SweepArgs) + 7) / 8];
+    __shared__ __align__(16) uint64_t map_sh[sizeof(SmoothBatchMap) / 8];
+    __shared__ uint32_t first_sh;
+    __shared__ int lo_sh;
+    SweepArgs &a = *reinterpret_cast<SweepArgs *>(args_sh);
     const uint32_t b = blockIdx.x;
-    int lo = 0;
-    for (int hi = n; hi - lo > 1;) {
-        const int mid = (lo + hi) >> 1;
-        if (block_start[mid] <= b) lo = mid;
-        else hi = mid;
+    const int lo = find_map_cta(block_start, n, b, &lo_sh);
+    load_map(reinterpret_cast<SmoothBatchMap *>(map_sh), maps + lo);
+    if (threadIdx.x == 0) {
+        const SmoothBatchMap &mp = *reinterpret_cast<const SmoothBatchMap *>(map_sh);
+        a.oin = mp.buf[t & 1];
+        a.oout = mp.buf[(t & 1) ^ 1];
+        a.nbr = mp.m.nbr;
+        a.nbrp = mp.m.nbrp;
+        a.rec = mp.m.rec;
+        a.by = mp.m.by;
+        a.bz = mp.m.bz;
+        a.soff = mp.m.sten_off;
+        a.sids = mp.m.sten_ids;
+        a.fmask = mp.m.face_mask;
+        a.meta = mp.m.meta;
+        a.cells = mp.m.cells;
+        a.cell_wide = mp.m.cell_wide;
+        a.cell_sy = mp.m.cell_sy;
+        a.cell_sz = mp.m.cell_sz;
+        a.lut_x = mp.m.lut_x;
+        a.lut_y = mp.m.lut_y;
+        a.lut_z = mp.m.lut_z;
+        a.points = mp.m.points;
+        a.np = mp.np;
+        a.lam = lam;
+        a.h = h;
+        a.spx = mp.spx;
+        a.spy = mp.spy;
+        a.spz = mp.spz;
+        a.first = t == 0;
+        a.last = t == launches - 1;
+        a.sphere = sphere;
+        a.ahead = 0;
+        first_sh = (b - block_start[lo]) * (uint32_t)kSweepPoints;
     }
-    const SmoothBatchMap &mp = maps[lo];
-    SweepArgs a;
-    a.oin = mp.buf[t & 1];
-    a.oout = mp.buf[(t & 1) ^ 1];
-    a.nbr = mp.m.nbr;
-    a.nbrp = mp.m.nbrp;
-    a.rec = mp.m.rec;
-    a.by = mp.m.by;
-    a.bz = mp.m.bz;
-    a.soff = mp.m.sten_off;
-    a.sids = mp.m.sten_ids;
-    a.fmask = mp.m.face_mask;
-    a.meta = mp.m.meta;
-    a.cells = mp.m.cells;
-    a.cell_wide = mp.m.cell_wide;
-    a.cell_sy = mp.m.cell_sy;
-    a.cell_sz = mp.m.cell_sz;
-    a.lut_x = mp.m.lut_x;
-    a.lut_y = mp.m.lut_y;
-    a.lut_z = mp.m.lut_z;
-    a.points = mp.m.points;
-    a.np = mp.np;
-    a.lam = lam;
-    a.h = h;
-    a.spx = mp.spx;
-    a.spy = mp.spy;
-    a.spz = mp.spz;
-    a.first = t == 0;
-    a.last = t == launches - 1;
-    a.sphere = sphere;
-    a.ahead = 0;
-    sweep_block<false, FUSED>(a, (b - block_start[lo]) * (uint32_t)kSweepPoints);
+    __syncthreads();
+    sweep_block<false, FUSED>(a, first_sh);
 }
 
 __global__ void __launch_bounds__(256) k_cells64(MeshArrays m, int64_t np, uint64_t *out)
@@ -295,15 +303,23 @@ cudaError_t launch_smooth_batch(const SmoothBatchMap *maps, const uint32_t *bloc
 {
     if (n_maps == 0 || total_blocks == 0) return cudaSuccess;
     const int launches = sweep_launches(iterations, fusable);
+    // launches after the first are programmatic dependents of the one before (as in launch_sweep)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(total_blocks);
+    cfg.blockDim = dim3(kSweepThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
     for (int t = 0; t < launches; ++t) {
         ProfScope ps("k_smooth_batch", st);
-        if (t == 0 && fusable && iterations >= 2)
-            k_smooth_batch<true><<<total_blocks, kSweepThreads, 0, st>>>(maps, block_start, n_maps, t, launches,
-                                                                         relaxation, half, sphere);
-        else
-            k_smooth_batch<false><<<total_blocks, kSweepThreads, 0, st>>>(maps, block_start, n_maps, t, launches,
-                                                                          relaxation, half, sphere);
-        cudaError_t e = cudaGetLastError();
+        cfg.numAttrs = t > 0 ? 1 : 0;
+        const bool fused = t == 0 && fusable && iterations >= 2;
+        cudaError_t e = fused ? cudaLaunchKernelEx(&cfg, k_smooth_batch<true>, maps, block_start, n_maps, t, launches,
+                                                   relaxation, half, sphere)
+                              : cudaLaunchKernelEx(&cfg, k_smooth_batch<false>, maps, block_start, n_maps, t,
+                                                   launches, relaxation, half, sphere);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -23,6 +23,14 @@ def run_gpu(labels, spacing=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0), selected=No
         up = sn.sn_labels_upload(np.ascontiguousarray(labels))
         m = sn.sn_extract_labels(up, spacing, origin, selected=selected, background=background)
         up.free()
+    elif on_device == "offset":  # device labels one element into a buffer: off every 16-byte boundary
+        a = np.ascontiguousarray(labels)
+        flat = np.zeros(a.size + 1, a.dtype)
+        flat[1:] = a.ravel()
+        t = torch.from_numpy(flat.view({1: np.uint8, 2: np.int16, 4: np.int32}[a.dtype.itemsize])).cuda()
+        t = t.view({1: torch.uint8, 2: torch.uint16, 4: torch.uint32}[a.dtype.itemsize])
+        src = t[1:].view(a.shape)
+        assert src.data_ptr() % 16 != 0
     elif on_device:
         t = torch.from_numpy(np.ascontiguousarray(labels).view(
             {1: np.uint8, 2: np.int16, 4: np.int32}[labels.dtype.itemsize])).cuda()

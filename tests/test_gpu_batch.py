@@ -102,6 +102,29 @@ def test_batch_equals_single_map_calls(graph, tune):
             np.testing.assert_array_equal(got[k], want[k], err_msg=k)
 
 
+def test_graph_batches_of_one_layout_with_new_contents():
+    """Graph mode keeps one executable graph per layout and updates it with the
+    next call's buffers and grid sizes: contents that differ between calls
+    (rolled and relabelled volumes of the same shapes) still match single calls."""
+    sn = _sn()
+    base = [sn_synth.config5_map(i).labels for i in range(6)]
+    for turn in range(3):
+        labs = [np.ascontiguousarray(np.roll(b, 3 * turn + i, axis=i % 3)) for i, b in enumerate(base)]
+        if turn == 2:
+            labs = [np.where(b > 0, (b.astype(np.int64) * 7 + 1) % 250 + 1, 0).astype(b.dtype) for b in labs]
+        dev = [_dev(b) for b in labs]
+        meshes = sn.sn_extract_smooth_batch(dev, iterations=8, relaxation=0.5, constraint_distance=1.0, graph=True)
+        for t, m in zip(dev, meshes):
+            got = _host(m)
+            m.free()
+            one = sn.sn_extract(t)
+            sn.sn_smooth(one, 8, 0.5, 1.0)
+            want = _host(one)
+            one.free()
+            for k in want:
+                np.testing.assert_array_equal(got[k], want[k], err_msg=k)
+
+
 def test_degenerate_batches():
     sn = _sn()
     assert sn.sn_extract_smooth_batch([]) == []

@@ -63,6 +63,35 @@ def test_packed_rows_with_words_not_dividing_a_warp(dtype, nx):
     parity(lab, selected=[1], background=0, iterations=2)
 
 
+@pytest.mark.parametrize("dtype,nx", [(np.uint8, 17), (np.uint8, 45), (np.uint8, 145), (np.uint8, 1001),
+                                      (np.uint16, 9), (np.uint16, 73), (np.uint16, 257), (np.uint32, 5),
+                                      (np.uint32, 67), (np.uint32, 301)])
+def test_rows_off_16_byte_boundaries(dtype, nx):
+    """Rows whose length is not a multiple of 16 bytes: the counting tile copies the 16-byte aligned span around
+    each slice block (its start moves from slice to slice) and moves the rows to a 16-byte pitch before the
+    packed compares.  70 rows and 19 slices span several row tiles and z-tiles; the selected-label form
+    classifies the moved rows."""
+    lab = sn_synth.ellipsoids((nx, 70, 19), 6, 3.0, 12.0, dtype, seed=nx)
+    parity(lab, iterations=4)
+    parity(lab, selected=[1, 3], iterations=2)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16, np.uint32])
+def test_labels_starting_off_16_byte_boundaries(dtype):
+    """A label map one element into its buffer: rows of 64 samples, but no row on a 16-byte boundary."""
+    lab = sn_synth.ellipsoids((64, 50, 21), 5, 3.0, 12.0, dtype, seed=7)
+    parity(lab, iterations=3, on_device="offset")
+
+
+def test_long_unaligned_rows_use_the_scalar_counting_form():
+    """uint32 rows of 8404 bytes: too long for the staged form within a slot, so the tile copies and compares
+    them element by element (and the emission uses the per-row kernels: 66 words per row)."""
+    rng = np.random.default_rng(5)
+    lab = (rng.random((4, 5, 2101)) < 0.2).astype(np.uint32) * rng.integers(1, 9, size=(4, 5, 2101)).astype(
+        np.uint32)
+    parity(lab, iterations=2)
+
+
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16, np.uint32])
 def test_uploaded_labels(dtype):
     """Labels copied ahead by sn_labels_upload, then extracted by sn_extract_labels."""
