@@ -720,7 +720,7 @@ def run_label_sweep(args):
 def batch_object(args, steps=None, loop=True):
     """The 256 seeded maps of uneven sizes (edges 32-256, uint8/uint16): a step is extract + 16 sweeps of every
     map.  Timed with the host clock around the whole step (host work included) after a device sync, for the
-    batched call (one launch per phase, tuned tile heights), the same with the graph (one executable graph per
+    batched call (one launch per phase, tuned tile shapes), the same with the graph (one executable graph per
     layout, updated in place), and a loop of single-map calls."""
     import torch
     import sn_synth
@@ -772,7 +772,7 @@ def batch_object(args, steps=None, loop=True):
                        "iterations": it, "timing": "host clock around each step (allocation, launches, waits)",
                        "batched": "sn_extract_smooth_batch: one counting launch per label type over all maps, one "
                                   "scan launch, one totals wait, one emission launch per label type, one sweep "
-                                  "launch per iteration over all maps, tuned emission tiles"},
+                                  "launch per iteration over all maps, tuned counting and emission tiles"},
             "graph_mode_ms_per_step": ms_graph, "graph_mode_gvoxels_s": V / (ms_graph / 1e3) / 1e9,
             "single_map_loop_ms_per_step": ms_loop,
             "single_map_loop_gvoxels_s": V / (ms_loop / 1e3) / 1e9 if ms_loop else None,

@@ -228,10 +228,13 @@ sn_status sn_mesh_triangles(const sn_mesh *m, const int32_t **triangles);
  *               into one CUDA graph and launch it once (one executable graph
  *               is kept per layout of maps -- sizes, types, sweeps -- per host
  *               thread, and updated in place on the next call of that layout);
- *               SN_BATCH_TUNE: choose the emission tile height per (label
- *               type, words per row, size class of rows and slices) by timing
- *               the candidates 8/16/24/32 on the first map of each class
- *               (cached for the process; results do not depend on it)
+ *               SN_BATCH_TUNE: choose the counting tile shape (label bytes
+ *               per slot, which fixes the rows per tile, and slices per tile)
+ *               and the emission tile height (8/16/24/32 cell rows or each
+ *               map's default) by timing the batched launches of the
+ *               candidates on the batch itself, once per batch layout (maps'
+ *               sizes and types; cached for the process; results do not
+ *               depend on it)
  *   out         sn_mesh* [n_maps]: each mesh is what sn_extract + sn_smooth
  *               give for that map, on cuda_stream, freed with sn_free.
  * Returns after the work is enqueued.  On an error no mesh is returned.

@@ -1559,62 +1559,24 @@ struct DeviceTables {
     }
 };
 
-// Tile height of the emission per (label type, words per row, cell rows, cell
-// slices) bucket, chosen by timing the candidates on the first map of the bucket.
+// Tile height of a batch's emission (cell rows per tile; 0: each map's default)
+// per batch layout, chosen with SN_BATCH_TUNE among these candidates.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int64_t, int64_t, int64_t>, int> g_tune;
-const int kTuneRows[] = {8, 16, 24, 32};
+std::map<uint64_t, int> g_tune_emit;
+const int kTuneRows[] = {0, 8, 16, 24, 32};
 
-std::tuple<int, int64_t, int64_t, int64_t> tune_key(const ExtractJob &j)
-{
-    auto bucket = [](int64_t v) { return v <= 64 ? 64 : v <= 128 ? 128 : v <= 256 ? 256 : 512; };
-    return std::make_tuple((int)j.type, j.g.W, bucket(j.g.ny + 1), bucket(j.g.nz + 1));
-}
-
-sn_status tune_emit_rows(ExtractJob &j, cudaStream_t st, int *rows)
-{
-    const auto key = tune_key(j);
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune.find(key);
-        if (it != g_tune.end()) {
-            *rows = it->second;
-            return SN_OK;
-        }
-    }
-    cudaEvent_t a = nullptr, b = nullptr;
-    cudaError_t e = cudaEventCreate(&a);
-    if (e == cudaSuccess) e = cudaEventCreate(&b);
-    int best = 0;
-    float best_ms = 0.f;
-    for (int r : kTuneRows) {
-        if (e != cudaSuccess) break;
-        sn_status st1 = job_emit(j, st, r); // warm-up and check
-        if (st1 != SN_OK) {
-            if (a) cudaEventDestroy(a);
-            if (b) cudaEventDestroy(b);
-            return st1;
-        }
-        e = cudaEventRecord(a, st);
-        for (int k = 0; k < 3 && e == cudaSuccess; ++k)
-            if (job_emit(j, st, r) != SN_OK) e = cudaErrorUnknown;
-        if (e == cudaSuccess) e = cudaEventRecord(b, st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(b);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-        if (e == cudaSuccess && (best == 0 || ms < best_ms)) {
-            best = r;
-            best_ms = ms;
-        }
-    }
-    if (a) cudaEventDestroy(a);
-    if (b) cudaEventDestroy(b);
-    if (e != cudaSuccess) return cuda_fail(e, "emission tuning");
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = best;
-    *rows = best;
-    return SN_OK;
-}
+// Counting tile shape of a batch: the label bytes a slot holds (which fixes the
+// rows per tile) and the slices per tile, at least.  With SN_BATCH_TUNE it is
+// chosen per batch layout by timing the batched counting launches of the
+// candidates on the batch itself: a small map timed alone favours short tiles
+// that fill the GPU by themselves, while in a batch the other maps fill it.
+// The counting pass only overwrites what it writes (planes, row counts), so a
+// candidate's run leaves nothing behind.
+struct CountShape {
+    int slot_kb, min_kz;
+};
+const CountShape kCountShapes[] = {{16, 16}, {16, 4}, {32, 16}, {32, 4}, {8, 16}, {16, 32}};
+std::map<uint64_t, CountShape> g_tune_count; // by batch layout
 
 } // namespace
 
@@ -1645,6 +1607,7 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
     std::vector<ExtractJob> jobs((size_t)n_maps);
     sn::DevTotals *htot = nullptr;
     cudaGraph_t graph = nullptr;
+    std::vector<cudaEvent_t> events;
     bool capturing = false;
     auto finish = [&](sn_status r) {
         if (capturing) {
@@ -1663,7 +1626,13 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
             if (r == SN_OK) j.mesh = nullptr; // handed out
             job_release(j, st);
         }
+        for (cudaEvent_t ev : events) cudaEventDestroy(ev);
         return r;
+    };
+    auto event = [&](cudaEvent_t *ev) -> cudaError_t {
+        const cudaError_t e2 = cudaEventCreate(ev);
+        if (e2 == cudaSuccess) events.push_back(*ev);
+        return e2;
     };
     const double one[3] = {1.0, 1.0, 1.0}, zero[3] = {0.0, 0.0, 0.0};
 
@@ -1722,39 +1691,119 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
             std::vector<uint32_t> start;
             uint64_t blocks = 0;
             size_t smem = 0;
-        } groups[3][2];
+        };
+        static const sn_label_type kTypes[3] = {SN_U8, SN_U16, SN_U32};
         std::vector<int64_t> two_kernel;
+        // the batched counting launches of all maps with one tile shape (tables freed with the jobs)
+        auto count_all = [&](const CountShape &shape, bool record_two_kernel) -> sn_status {
+            CountGroup groups[3][2];
+            for (int64_t i = 0; i < n_maps; ++i) {
+                ExtractJob &j = jobs[i];
+                sn::CountTiling tl;
+                size_t smem = 0;
+                const int ti = j.type == SN_U8 ? 0 : j.type == SN_U16 ? 1 : 2;
+                bool batched = j.cls.mode == sn::CLASS_ALL &&
+                               sn::count_tiling(j.type, j.dlabels, j.g, &tl, &smem, shape.slot_kb, shape.min_kz);
+                if (batched) {
+                    CountGroup &G = groups[ti][tl.aligned ? 1 : 0];
+                    sn::CountBatchMap d;
+                    std::memset(&d, 0, sizeof(d));
+                    d.lab = j.dlabels;
+                    d.c = j.cls;
+                    d.g = j.g;
+                    d.s = j.s;
+                    d.tl = tl;
+                    d.tot = j.dtot;
+                    d.gx = (j.g.ny + tl.ty - 1) / tl.ty;
+                    const uint64_t nb = (uint64_t)d.gx * (uint64_t)(tl.zt1 - tl.zt0);
+                    batched = G.blocks + nb <= 0x7fffffffull;
+                    if (batched) {
+                        G.start.push_back((uint32_t)G.blocks);
+                        G.blocks += nb;
+                        G.maps.push_back(d);
+                        G.smem = std::max(G.smem, smem);
+                    }
+                }
+                if (!batched && record_two_kernel) two_kernel.push_back(i);
+            }
+            DeviceTables tabs;
+            size_t at[3][2][2] = {};
+            for (int ti = 0; ti < 3; ++ti)
+                for (int f = 0; f < 2; ++f)
+                    if (!groups[ti][f].maps.empty()) {
+                        at[ti][f][0] = tabs.add(groups[ti][f].maps);
+                        at[ti][f][1] = tabs.add(groups[ti][f].start);
+                    }
+            char *dt = nullptr;
+            sn_status r = tabs.upload(&dt, jobs[0].pool, st, "batch counting tables");
+            if (r != SN_OK) return r;
+            jobs[0].temps.push_back(dt);
+            for (int ti = 0; ti < 3; ++ti)
+                for (int f = 0; f < 2; ++f) {
+                    const CountGroup &G = groups[ti][f];
+                    if (G.maps.empty()) continue;
+                    const cudaError_t e2 = sn::launch_count_batch(
+                        kTypes[ti], f == 1, reinterpret_cast<const sn::CountBatchMap *>(dt + at[ti][f][0]),
+                        reinterpret_cast<const uint32_t *>(dt + at[ti][f][1]), (int)G.maps.size(), (uint32_t)G.blocks,
+                        G.smem, st);
+                    if (e2 != cudaSuccess) return cuda_fail(e2, "batched counting launch");
+                }
+            return SN_OK;
+        };
+        CountShape shape = {kBatchSlotKB, kBatchMinKz};
+        if (flags & SN_BATCH_TUNE) {
+            uint64_t key = mix64(0xc0417ull + (uint64_t)n_maps) ^ mix64((uint64_t)dev);
+            for (int64_t i = 0; i < n_maps; ++i)
+                key = mix64(key ^ (uint64_t)jobs[i].dims[0] ^ ((uint64_t)jobs[i].dims[1] << 21) ^
+                            ((uint64_t)jobs[i].dims[2] << 42) ^ ((uint64_t)jobs[i].type << 62) ^
+                            (((uintptr_t)jobs[i].dlabels & 15) ? 0x9e37ull : 0ull));
+            bool cached = false;
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                auto it = g_tune_count.find(key);
+                if ((cached = it != g_tune_count.end())) shape = it->second;
+            }
+            if (!cached) {
+                cudaEvent_t ta = nullptr, tb = nullptr;
+                if ((e = event(&ta)) != cudaSuccess || (e = event(&tb)) != cudaSuccess)
+                    return finish(cuda_fail(e, "counting tile tuning"));
+                float best_ms = -1.f;
+                for (const CountShape &c : kCountShapes) {
+                    sn_status r = count_all(c, false); // warm-up
+                    if (r == SN_OK && (e = cudaEventRecord(ta, st)) != cudaSuccess) r = cuda_fail(e, "tuning");
+                    for (int k = 0; k < 2 && r == SN_OK; ++k) r = count_all(c, false);
+                    if (r == SN_OK && ((e = cudaEventRecord(tb, st)) != cudaSuccess ||
+                                       (e = cudaEventSynchronize(tb)) != cudaSuccess))
+                        r = cuda_fail(e, "tuning");
+                    if (r != SN_OK) return finish(r);
+                    float ms = 0.f;
+                    if ((e = cudaEventElapsedTime(&ms, ta, tb)) != cudaSuccess)
+                        return finish(cuda_fail(e, "counting tile tuning"));
+                    if (best_ms < 0.f || ms < best_ms) {
+                        best_ms = ms;
+                        shape = c;
+                    }
+                }
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tune_count[key] = shape;
+            }
+        }
+        {
+            const sn_status r = count_all(shape, true);
+            if (r != SN_OK) return finish(r);
+        }
+        for (int64_t i : two_kernel) {
+            ExtractJob &j = jobs[i];
+            if ((e = sn::launch_planes(j.type, j.dlabels, j.cls, j.g, j.s, st)) != cudaSuccess ||
+                (e = sn::launch_cellrows(j.g, j.s, st)) != cudaSuccess)
+                return finish(cuda_fail(e, "counting launch"));
+        }
+        // the row scans of all maps in one launch
         std::vector<sn::ScanBatchMap> scans((size_t)n_maps);
         std::vector<uint32_t> scan_start((size_t)n_maps);
         uint64_t scan_blocks = 0;
         for (int64_t i = 0; i < n_maps; ++i) {
-            ExtractJob &j = jobs[i];
-            sn::CountTiling tl;
-            size_t smem = 0;
-            const int ti = j.type == SN_U8 ? 0 : j.type == SN_U16 ? 1 : 2;
-            bool batched = j.cls.mode == sn::CLASS_ALL &&
-                           sn::count_tiling(j.type, j.dlabels, j.g, &tl, &smem, kBatchSlotKB, kBatchMinKz);
-            if (batched) {
-                CountGroup &G = groups[ti][tl.aligned ? 1 : 0];
-                sn::CountBatchMap d;
-                std::memset(&d, 0, sizeof(d));
-                d.lab = j.dlabels;
-                d.c = j.cls;
-                d.g = j.g;
-                d.s = j.s;
-                d.tl = tl;
-                d.tot = j.dtot;
-                d.gx = (j.g.ny + tl.ty - 1) / tl.ty;
-                const uint64_t nb = (uint64_t)d.gx * (uint64_t)(tl.zt1 - tl.zt0);
-                batched = G.blocks + nb <= 0x7fffffffull;
-                if (batched) {
-                    G.start.push_back((uint32_t)G.blocks);
-                    G.blocks += nb;
-                    G.maps.push_back(d);
-                    G.smem = std::max(G.smem, smem);
-                }
-            }
-            if (!batched) two_kernel.push_back(i);
+            const ExtractJob &j = jobs[i];
             sn::ScanBatchMap &sc = scans[i];
             std::memset(&sc, 0, sizeof(sc));
             sc.g = j.g;
@@ -1765,36 +1814,12 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
             scan_blocks += (uint64_t)sc.ntiles;
         }
         if (scan_blocks > 0x7fffffffull) return finish(fail(SN_EINVAL, "too many cell rows in one batch"));
-        // the tables in one device block (one copy from pageable memory: the vectors may go once it returns)
         DeviceTables tabs;
-        size_t at_count[3][2][2] = {}, at_scan = tabs.add(scans), at_scan_start = tabs.add(scan_start);
-        for (int ti = 0; ti < 3; ++ti)
-            for (int f = 0; f < 2; ++f)
-                if (!groups[ti][f].maps.empty()) {
-                    at_count[ti][f][0] = tabs.add(groups[ti][f].maps);
-                    at_count[ti][f][1] = tabs.add(groups[ti][f].start);
-                }
+        const size_t at_scan = tabs.add(scans), at_scan_start = tabs.add(scan_start);
         char *dt = nullptr;
-        sn_status r = tabs.upload(&dt, jobs[0].pool, st, "batch counting tables");
+        sn_status r = tabs.upload(&dt, jobs[0].pool, st, "batch scan tables");
         if (r != SN_OK) return finish(r);
         jobs[0].temps.push_back(dt);
-        static const sn_label_type kTypes[3] = {SN_U8, SN_U16, SN_U32};
-        for (int ti = 0; ti < 3; ++ti)
-            for (int f = 0; f < 2; ++f) {
-                const CountGroup &G = groups[ti][f];
-                if (G.maps.empty()) continue;
-                e = sn::launch_count_batch(kTypes[ti], f == 1,
-                                           reinterpret_cast<const sn::CountBatchMap *>(dt + at_count[ti][f][0]),
-                                           reinterpret_cast<const uint32_t *>(dt + at_count[ti][f][1]),
-                                           (int)G.maps.size(), (uint32_t)G.blocks, G.smem, st);
-                if (e != cudaSuccess) return finish(cuda_fail(e, "batched counting launch"));
-            }
-        for (int64_t i : two_kernel) {
-            ExtractJob &j = jobs[i];
-            if ((e = sn::launch_planes(j.type, j.dlabels, j.cls, j.g, j.s, st)) != cudaSuccess ||
-                (e = sn::launch_cellrows(j.g, j.s, st)) != cudaSuccess)
-                return finish(cuda_fail(e, "counting launch"));
-        }
         e = sn::launch_scan_batch(reinterpret_cast<const sn::ScanBatchMap *>(dt + at_scan),
                                   reinterpret_cast<const uint32_t *>(dt + at_scan_start), (int)n_maps,
                                   (uint32_t)scan_blocks, st);
@@ -1805,15 +1830,116 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
     if (e != cudaSuccess) return finish(cuda_fail(e, "count read-back"));
 
     // 3. exact outputs and smoothing buffers (main stream); tile heights
-    std::vector<int> rows((size_t)n_maps, 0);
     for (int64_t i = 0; i < n_maps; ++i) {
         sn_status r = job_allocate(jobs[i], st, iterations > 0);
         if (r != SN_OK) return finish(r);
-        if (flags & SN_BATCH_TUNE) {
-            r = tune_emit_rows(jobs[i], st, &rows[i]);
-            if (r != SN_OK) return finish(r);
+    }
+
+    // the batched emission's tiles, per label type (maps whose rows fit an emission tile);
+    // rows = cell rows per tile of every map (0: each map's default)
+    struct EmitGroup {
+        std::vector<sn::EmitBatchMap> maps;
+        std::vector<uint32_t> start;
+        uint64_t blocks = 0;
+        size_t smem = 0;
+        size_t at_maps = 0, at_start = 0;
+    };
+    static const sn_label_type kEmitTypes[3] = {SN_U8, SN_U16, SN_U32};
+    auto emit_groups = [&](int rows, EmitGroup (&groups)[3], std::vector<int64_t> *single) {
+        for (int64_t i = 0; i < n_maps; ++i) {
+            const ExtractJob &j = jobs[i];
+            const sn_mesh *m = j.mesh;
+            sn::TileGeom tg;
+            size_t smem = 0;
+            const int ti = j.type == SN_U8 ? 0 : j.type == SN_U16 ? 1 : 2;
+            bool batched = j.cls.mode == sn::CLASS_ALL && sn::emit_tiling(j.g, rows, m->np + m->nq, &tg, &smem) &&
+                           smem + 32 + sizeof(sn::EmitBatchMap) <= 227 * 1024;
+            if (batched) {
+                EmitGroup &G = groups[ti];
+                sn::EmitBatchMap d;
+                std::memset(&d, 0, sizeof(d));
+                d.lab = j.dlabels;
+                d.c = j.cls;
+                d.g = j.g;
+                d.s = j.s;
+                d.m = m->a;
+                d.tot = j.dtot;
+                d.tg = tg;
+                d.gx = (j.g.ny + 1 + tg.ty - 1) / tg.ty;
+                const uint64_t nb = (uint64_t)d.gx * (uint64_t)(j.g.nz + 1);
+                batched = G.blocks + nb <= 0x7fffffffull;
+                if (batched) {
+                    G.start.push_back((uint32_t)G.blocks);
+                    G.blocks += nb;
+                    G.maps.push_back(d);
+                    G.smem = std::max(G.smem, smem);
+                }
+            }
+            if (!batched && single) single->push_back(i);
+        }
+    };
+    auto emit_launch = [&](const EmitGroup (&groups)[3], const char *dt, cudaStream_t s2) -> cudaError_t {
+        for (int ti = 0; ti < 3; ++ti) {
+            const EmitGroup &G = groups[ti];
+            if (G.maps.empty()) continue;
+            const cudaError_t e2 = sn::launch_emit_tile_batch(
+                kEmitTypes[ti], reinterpret_cast<const sn::EmitBatchMap *>(dt + G.at_maps),
+                reinterpret_cast<const uint32_t *>(dt + G.at_start), (int)G.maps.size(), (uint32_t)G.blocks, G.smem,
+                s2);
+            if (e2 != cudaSuccess) return e2;
+        }
+        return cudaSuccess;
+    };
+    // SN_BATCH_TUNE: the tile height of the batch's emission, chosen per batch layout by timing
+    // the batched emission launches of the candidates (the emission only overwrites its outputs)
+    int emit_rows = 0;
+    if (flags & SN_BATCH_TUNE) {
+        uint64_t key = mix64(0xe317ull + (uint64_t)n_maps) ^ mix64((uint64_t)dev);
+        for (int64_t i = 0; i < n_maps; ++i)
+            key = mix64(key ^ (uint64_t)jobs[i].dims[0] ^ ((uint64_t)jobs[i].dims[1] << 21) ^
+                        ((uint64_t)jobs[i].dims[2] << 42) ^ ((uint64_t)jobs[i].type << 62));
+        bool cached = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_emit.find(key);
+            if ((cached = it != g_tune_emit.end())) emit_rows = it->second;
+        }
+        if (!cached) {
+            cudaEvent_t ta = nullptr, tb = nullptr;
+            if ((e = event(&ta)) != cudaSuccess || (e = event(&tb)) != cudaSuccess)
+                return finish(cuda_fail(e, "emission tuning"));
+            float best_ms = -1.f;
+            for (int cand : kTuneRows) {
+                EmitGroup cg[3];
+                emit_groups(cand, cg, nullptr);
+                DeviceTables ct;
+                for (auto &G : cg)
+                    if (!G.maps.empty()) {
+                        G.at_maps = ct.add(G.maps);
+                        G.at_start = ct.add(G.start);
+                    }
+                char *cdt = nullptr;
+                sn_status r = ct.upload(&cdt, jobs[0].pool, st, "emission tuning tables");
+                if (r != SN_OK) return finish(r);
+                jobs[0].temps.push_back(cdt);
+                e = emit_launch(cg, cdt, st); // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(ta, st);
+                for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = emit_launch(cg, cdt, st);
+                if (e == cudaSuccess) e = cudaEventRecord(tb, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(tb);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ta, tb);
+                if (e != cudaSuccess) return finish(cuda_fail(e, "emission tuning"));
+                if (best_ms < 0.f || ms < best_ms) {
+                    best_ms = ms;
+                    emit_rows = cand;
+                }
+            }
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_emit[key] = emit_rows;
         }
     }
+    std::vector<int> rows((size_t)n_maps, emit_rows);
 
     // the tables of the launches below, uploaded in one piece: the prologue (cell-centre
     // tables, meta words) and epilogue (last stencil offsets) of all meshes, the batched
@@ -1842,45 +1968,9 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
         }
         at_prep = tabs.add(tab);
     }
-    struct EmitGroup {
-        std::vector<sn::EmitBatchMap> maps;
-        std::vector<uint32_t> start;
-        uint64_t blocks = 0;
-        size_t smem = 0;
-        size_t at_maps = 0, at_start = 0;
-    } egroups[3];
+    EmitGroup egroups[3];
     std::vector<int64_t> emit_single;
-    for (int64_t i = 0; i < n_maps; ++i) {
-        const ExtractJob &j = jobs[i];
-        const sn_mesh *m = j.mesh;
-        sn::TileGeom tg;
-        size_t smem = 0;
-        const int ti = j.type == SN_U8 ? 0 : j.type == SN_U16 ? 1 : 2;
-        bool batched = j.cls.mode == sn::CLASS_ALL && sn::emit_tiling(j.g, rows[i], m->np + m->nq, &tg, &smem) &&
-                       smem + 32 + sizeof(sn::EmitBatchMap) <= 227 * 1024;
-        if (batched) {
-            EmitGroup &G = egroups[ti];
-            sn::EmitBatchMap d;
-            std::memset(&d, 0, sizeof(d));
-            d.lab = j.dlabels;
-            d.c = j.cls;
-            d.g = j.g;
-            d.s = j.s;
-            d.m = m->a;
-            d.tot = j.dtot;
-            d.tg = tg;
-            d.gx = (j.g.ny + 1 + tg.ty - 1) / tg.ty;
-            const uint64_t nb = (uint64_t)d.gx * (uint64_t)(j.g.nz + 1);
-            batched = G.blocks + nb <= 0x7fffffffull;
-            if (batched) {
-                G.start.push_back((uint32_t)G.blocks);
-                G.blocks += nb;
-                G.maps.push_back(d);
-                G.smem = std::max(G.smem, smem);
-            }
-        }
-        if (!batched) emit_single.push_back(i);
-    }
+    emit_groups(emit_rows, egroups, &emit_single);
     for (auto &G : egroups)
         if (!G.maps.empty()) {
             G.at_maps = tabs.add(G.maps);
@@ -1937,15 +2027,7 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
     if ((e = sn::launch_prologue_batch(prep, (int)n_maps, prep_entries, origin_st)) != cudaSuccess)
         return finish(cuda_fail(e, "batch prologue"));
     const float half = 0.5f * constraint_distance;
-    static const sn_label_type kEmitTypes[3] = {SN_U8, SN_U16, SN_U32};
-    for (int ti = 0; ti < 3; ++ti) {
-        const EmitGroup &G = egroups[ti];
-        if (G.maps.empty()) continue;
-        e = sn::launch_emit_tile_batch(kEmitTypes[ti], reinterpret_cast<const sn::EmitBatchMap *>(dt + G.at_maps),
-                                       reinterpret_cast<const uint32_t *>(dt + G.at_start), (int)G.maps.size(),
-                                       (uint32_t)G.blocks, G.smem, origin_st);
-        if (e != cudaSuccess) return finish(cuda_fail(e, "batched emission launch"));
-    }
+    if ((e = emit_launch(egroups, dt, origin_st)) != cudaSuccess) return finish(cuda_fail(e, "batched emission launch"));
     for (int64_t i : emit_single) {
         sn_status r = job_emit(jobs[i], origin_st, rows[i], true);
         if (r != SN_OK) return finish(r);
