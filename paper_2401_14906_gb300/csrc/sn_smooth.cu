@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) k_centres(MeshArrays m, int64_t np)
 template <bool FUSED>
 __global__ void __launch_bounds__(kSweepThreads, 2048 / kSweepThreads)
     k_smooth_batch(const SmoothBatchMap *maps, const uint32_t *block_start, int n, int t, int launches, float lam,
-                   float h, int sphere)
+                   float h, int sphere, uint32_t ahead)
 {
     __shared__ __align__(16) uint64_t args_sh[(sizeof(SweepArgs) + 7) / 8];
     __shared__ __align__(16) uint64_t map_sh[sizeof(SmoothBatchMap) / 8];
@@ -83,6 +83,29 @@ __global__ void __launch_bounds__(kSweepThreads, 2048 / kSweepThreads)
         first_sh = (b - block_start[lo]) * (uint32_t)kSweepPoints;
     }
     __syncthreads();
+    // Prefetch into L2 the streamed inputs (records, and the offsets of sweeps that read
+    // them) of the block `ahead` blocks later -- about one wave of resident CTAs on, and
+    // often in another mesh -- as sweep_block does within one mesh.
+    if (SN_SWEEP_PREFETCH && ahead && threadIdx.x == 0 && b + ahead < gridDim.x) {
+        const uint32_t b2 = b + ahead;
+        int m2 = 0;
+        for (int hi = n; hi - m2 > 1;) {
+            const int mid = (m2 + hi) >> 1;
+            if (block_start[mid] <= b2) m2 = mid;
+            else hi = mid;
+        }
+        const SmoothBatchMap &q = maps[m2];
+        const uint64_t np2 = (uint64_t)q.np, nb0 = (uint64_t)(b2 - block_start[m2]) * kSweepPoints;
+        if (nb0 < np2) {
+            const uint64_t cnt = np2 - nb0 < (uint64_t)kSweepPoints ? np2 - nb0 : (uint64_t)kSweepPoints;
+            const uint32_t rb = (uint32_t)((cnt * 8ull) & ~15ull), ob = (uint32_t)((cnt * 12ull) & ~15ull);
+            if (q.m.rec != REC_CSR && rb)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q.m.nbr + nb0), "r"(rb) : "memory");
+            if (t > 0 && ob)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q.buf[t & 1] + 3ull * nb0), "r"(ob)
+                             : "memory");
+        }
+    }
     sweep_block<false, FUSED>(a, first_sh);
 }
 
@@ -303,6 +326,7 @@ cudaError_t launch_smooth_batch(const SmoothBatchMap *maps, const uint32_t *bloc
 {
     if (n_maps == 0 || total_blocks == 0) return cudaSuccess;
     const int launches = sweep_launches(iterations, fusable);
+    const uint32_t ahead = sweep_ahead((int64_t)total_blocks * kSweepPoints);
     // launches after the first are programmatic dependents of the one before (as in launch_sweep)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(total_blocks);
@@ -317,9 +341,9 @@ cudaError_t launch_smooth_batch(const SmoothBatchMap *maps, const uint32_t *bloc
         cfg.numAttrs = t > 0 ? 1 : 0;
         const bool fused = t == 0 && fusable && iterations >= 2;
         cudaError_t e = fused ? cudaLaunchKernelEx(&cfg, k_smooth_batch<true>, maps, block_start, n_maps, t, launches,
-                                                   relaxation, half, sphere)
+                                                   relaxation, half, sphere, ahead)
                               : cudaLaunchKernelEx(&cfg, k_smooth_batch<false>, maps, block_start, n_maps, t,
-                                                   launches, relaxation, half, sphere);
+                                                   launches, relaxation, half, sphere, ahead);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
