@@ -745,25 +745,32 @@ def batch_object(args, steps=None, loop=True):
         torch.cuda.synchronize()
         return ms
 
-    def timed(fn):
+    per_step = {}
+
+    def timed(fn, name):
         for _ in range(max(3, min(args.warmup, 5))):
             for m in fn():
                 m.free()
         torch.cuda.synchronize()
+        marks = []
         t0 = time.perf_counter()
         for _ in range(steps):
-            for m in fn():
+            for m in fn():  # (each call ends with a device sync: the step's own end)
                 m.free()
+            marks.append(time.perf_counter())
         torch.cuda.synchronize()
-        return (time.perf_counter() - t0) * 1e3 / steps
+        total = (time.perf_counter() - t0) * 1e3 / steps
+        d = np.diff(np.array([t0] + marks)) * 1e3
+        per_step[name] = {"median": float(np.median(d)), "max": float(d.max())}
+        return total
 
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
-    ms_batch = timed(batched)
+    ms_batch = timed(batched, "batched")
     clocks = sampler.stop()
-    ms_graph = timed(lambda: batched(True))
-    ms_loop = timed(looped) if loop else None
+    ms_graph = timed(lambda: batched(True), "graph")
+    ms_loop = timed(looped, "loop") if loop else None
     counts = [m.counts for m in batched()]
     P = sum(c[0] for c in counts)
     return {"metric": METRIC, "value": V / (ms_batch / 1e3) / 1e9, "unit": UNIT, "steps": steps,
@@ -773,7 +780,9 @@ def batch_object(args, steps=None, loop=True):
                        "batched": "sn_extract_smooth_batch: one counting launch per label type over all maps, one "
                                   "scan launch, one totals wait, one emission launch per label type, one sweep "
                                   "launch per iteration over all maps, tuned counting and emission tiles"},
+            "ms_per_step_median": per_step["batched"]["median"], "ms_per_step_max": per_step["batched"]["max"],
             "graph_mode_ms_per_step": ms_graph, "graph_mode_gvoxels_s": V / (ms_graph / 1e3) / 1e9,
+            "graph_mode_ms_per_step_median": per_step["graph"]["median"],
             "single_map_loop_ms_per_step": ms_loop,
             "single_map_loop_gvoxels_s": V / (ms_loop / 1e3) / 1e9 if ms_loop else None,
             "clocks": clocks}
