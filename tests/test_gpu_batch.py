@@ -6,6 +6,11 @@
 * The first 48 maps against the single-map calls: bit-identical outputs (the
   same kernels run; tile heights and streams change nothing), with and without
   the graph and the tuner.
+* Graph mode over three calls of one layout with new contents (the update of
+  the kept executable graph).
+* One batch that takes every counting form (direct, staged, element-wise,
+  two-kernel) and both emission forms (batched tiles, map by map), uint32
+  included, against the oracle.
 * Degenerate batches: empty, maps without surfaces, host and device labels mixed.
 """
 import numpy as np
@@ -123,6 +128,44 @@ def test_graph_batches_of_one_layout_with_new_contents():
             one.free()
             for k in want:
                 np.testing.assert_array_equal(got[k], want[k], err_msg=k)
+
+
+@pytest.mark.parametrize("graph,tune", [(False, False), (True, True)])
+def test_batch_of_every_counting_and_emission_form(graph, tune):
+    """uint32 maps alongside uint8/uint16 ones, chosen so that one batch takes every form of the batched kernels and
+    their fallbacks (with the batch's 16 KB counting slots): rows on 16-byte boundaries (direct counting), rows off
+    them and a map one element into its buffer (staged counting), uint32 rows of 6004 bytes (element-wise counting),
+    of 8404 bytes (no counting tile fits: the two-kernel form; 66 words per row, so the emission runs map by map) and
+    of 20 KB (the same).  Every map against the FP64 oracle."""
+    import torch
+    sn = _sn()
+    rng = np.random.default_rng(77)
+    maps = [sn_synth.ellipsoids((64, 40, 23), 4, 3.0, 10.0, np.uint32, seed=1),
+            sn_synth.ellipsoids((67, 45, 19), 5, 3.0, 10.0, np.uint32, seed=2),
+            sn_synth.ellipsoids((33, 30, 28), 3, 3.0, 9.0, np.uint8, seed=3),
+            sn_synth.ellipsoids((75, 21, 17), 4, 2.5, 8.0, np.uint16, seed=4)]
+    for nx, ny, nz in ((1501, 4, 5), (2101, 4, 5), (5000, 3, 3)):
+        a = (rng.random((nz, ny, nx)) < 0.2).astype(np.uint32) * rng.integers(1, 9, size=(nz, ny, nx)).astype(
+            np.uint32)
+        maps.append(a)
+    devs = [_dev(m) for m in maps]
+    off = sn_synth.ellipsoids((48, 26, 20), 4, 3.0, 9.0, np.uint32, seed=5)
+    flat = torch.zeros(off.size + 1, dtype=torch.int32, device="cuda")
+    flat[1:] = torch.from_numpy(off.view(np.int32).ravel()).cuda()
+    devs.append(flat.view(torch.uint32)[1:].view(off.shape))
+    maps.append(off)
+    meshes = sn.sn_extract_smooth_batch(devs, iterations=6, relaxation=0.5, constraint_distance=1.0, graph=graph,
+                                        tune=tune)
+    for lab, m in zip(maps, meshes):
+        got = _host(m)
+        m.free()
+        ref = oracle.extract(lab)
+        assert got["points"].shape[0] == ref.n_points and got["quads"].shape[0] == ref.n_quads
+        for k, want in (("quads", ref.quads), ("quad_labels", ref.quad_labels), ("face_masks", ref.face_masks),
+                        ("stencil_offsets", ref.stencil_offsets), ("stencil_ids", ref.stencil_ids)):
+            np.testing.assert_array_equal(got[k], want, err_msg=k)
+        off_ref, pts_ref = oracle.smooth(ref, iterations=6, relaxation=0.5, constraint=1.0)
+        compare_smooth(got, off_ref, pts_ref, (1.0, 1.0, 1.0), 1.0)
 
 
 def test_degenerate_batches():
