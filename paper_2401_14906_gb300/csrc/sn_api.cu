@@ -193,7 +193,8 @@ void set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
 
 int scan_spin_limit() { return g_spin_limit.load(); }
 
-ProfScope::ProfScope(const char *name, cudaStream_t st) : name_(name), st_(st), a_(nullptr), b_(nullptr), on_(false)
+ProfScope::ProfScope(const char *name, cudaStream_t st)
+    : name_(name), st_(st), a_(nullptr), b_(nullptr), on_(false), range_(name)
 {
     if (!g_prof_on.load()) return;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -726,6 +727,7 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
                      const double origin[3], const uint32_t *selected, int64_t n_selected, uint32_t background,
                      void *cuda_stream, sn_mesh **out)
 {
+    sn::TraceRange trace_("sn_extract");
     g_last_error.clear();
     if (!out) return fail(SN_EINVAL, "out is NULL");
     *out = nullptr;
@@ -756,6 +758,7 @@ sn_status sn_extract(const void *labels, sn_label_type type, const int64_t dims[
 
 sn_status sn_labels_upload(const void *host_labels, sn_label_type type, const int64_t dims[3], sn_labels **out)
 {
+    sn::TraceRange trace_("sn_labels_upload");
     g_last_error.clear();
     if (!out) return fail(SN_EINVAL, "out is NULL");
     *out = nullptr;
@@ -807,6 +810,7 @@ sn_status sn_extract_labels(const sn_labels *labels, const double spacing[3], co
                             const uint32_t *selected, int64_t n_selected, uint32_t background, void *cuda_stream,
                             sn_mesh **out)
 {
+    sn::TraceRange trace_("sn_extract_labels");
     g_last_error.clear();
     if (out) *out = nullptr;
     if (!labels || !labels->data || !labels->uploaded) return fail(SN_EINVAL, "labels is NULL or not uploaded");
@@ -851,6 +855,7 @@ sn_status sn_smooth(sn_mesh *m, int iterations, float relaxation, float constrai
 sn_status sn_smooth_ex(sn_mesh *m, int iterations, float relaxation, float constraint_distance,
                        sn_constraint constraint)
 {
+    sn::TraceRange trace_("sn_smooth");
     g_last_error.clear();
     if (constraint != SN_CONSTRAINT_BOX && constraint != SN_CONSTRAINT_SPHERE)
         return fail(SN_EINVAL, "unknown constraint");
@@ -874,6 +879,7 @@ sn_status sn_smooth_ex(sn_mesh *m, int iterations, float relaxation, float const
 
 sn_status sn_triangulate(sn_mesh *m, sn_tri_method method)
 {
+    sn::TraceRange trace_("sn_triangulate");
     g_last_error.clear();
     if (!m) return fail(SN_EINVAL, "mesh is NULL");
     if (method != SN_TRI_GREEDY && method != SN_TRI_SHORTEST && method != SN_TRI_MIN_AREA && method != SN_TRI_COPLANAR)
@@ -1019,6 +1025,7 @@ sn_status sn_slab_stitch(const sn_mesh *m, const sn_slab_part *part, int64_t glo
 sn_status sn_mesh_copy_to_host(const sn_mesh *m, float *points, int32_t *quads, void *quad_labels,
                                int64_t *stencil_offsets, int32_t *stencil_ids, float *offsets)
 {
+    sn::TraceRange trace_("sn_mesh_copy_to_host");
     if (!m) return fail(SN_EINVAL, "mesh is NULL");
     if (points || offsets) {
         cudaError_t e0 = ensure_centres(m);
@@ -1099,6 +1106,7 @@ int32_t *meta_slot()
 sn_status sn_mesh_copy_to_host_async(sn_mesh *m, float *points, int32_t *quads, void *quad_labels,
                                      int64_t *stencil_offsets, int32_t *stencil_ids, float *offsets)
 {
+    sn::TraceRange trace_("sn_mesh_copy_to_host_async");
     g_last_error.clear();
     if (!m) return fail(SN_EINVAL, "mesh is NULL");
     cudaStream_t cs = d2h_stream(m->device);
@@ -1442,6 +1450,7 @@ sn_status sn_learner_train(sn_learner *l, int epochs, int64_t batch, float lr, f
 sn_status sn_smooth_learned(sn_mesh *m, const sn_learner *l, int corrections, float relaxation,
                             float constraint_distance, sn_constraint constraint)
 {
+    sn::TraceRange trace_("sn_smooth_learned");
     g_last_error.clear();
     if (!m) return fail(SN_EINVAL, "mesh is NULL");
     if (sn_status r = learner_check(l)) return r;
@@ -1587,6 +1596,7 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
                                   uint32_t background, int iterations, float relaxation, float constraint_distance,
                                   int flags, void *cuda_stream, sn_mesh **out)
 {
+    sn::TraceRange trace_("sn_extract_smooth_batch");
     g_last_error.clear();
     if (n_maps < 0 || (n_maps > 0 && (!labels || !types || !dims || !out)))
         return fail(SN_EINVAL, "n_maps < 0 or a NULL array");
@@ -1686,6 +1696,7 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
     //    alignment over the maps whose rows fit a counting tile (the two-kernel form for the
     //    rest, map by map), one scan launch over all maps, then one wait
     {
+        sn::TraceRange phase("batch: counting and scans");
         struct CountGroup {
             std::vector<sn::CountBatchMap> maps;
             std::vector<uint32_t> start;
@@ -1825,8 +1836,11 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
                                   (uint32_t)scan_blocks, st);
         if (e != cudaSuccess) return finish(cuda_fail(e, "batched scan launch"));
     }
-    e = cudaMemcpyAsync(htot, dtot_all, sizeof(sn::DevTotals) * (size_t)n_maps, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    {
+        sn::TraceRange phase("batch: totals wait");
+        e = cudaMemcpyAsync(htot, dtot_all, sizeof(sn::DevTotals) * (size_t)n_maps, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
     if (e != cudaSuccess) return finish(cuda_fail(e, "count read-back"));
 
     // 3. exact outputs and smoothing buffers (main stream); tile heights

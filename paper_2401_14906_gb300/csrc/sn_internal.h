@@ -14,6 +14,7 @@
 #include <atomic>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/sn.h"
@@ -317,6 +318,16 @@ cudaError_t launch_slab_shift(const MeshArrays &m, int64_t first_point, int64_t 
 void set_last_error(const char *msg);
 
 // profiling (sn_api.cu)
+// An NVTX range on the host timeline for the scope's lifetime (a no-op unless a
+// tracing tool is attached): API calls, batch phases and every kernel launch
+// the library makes (through ProfScope) show up by name in a timeline.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+
 struct ProfScope {
     ProfScope(const char *name, cudaStream_t st);
     ~ProfScope();
@@ -324,6 +335,7 @@ struct ProfScope {
     cudaStream_t st_;
     cudaEvent_t a_, b_;
     bool on_;
+    TraceRange range_;
 };
 
 } // namespace sn
