@@ -412,6 +412,16 @@ void sn_profile_enable(int on);
 int sn_profile_read(sn_kernel_time *out, int cap, int reset);
 
 /*
+ * sn_trim_memory -- device memory is taken from a per-device pool that keeps
+ * freed blocks for reuse (sn_free and the calls' temporaries return memory to
+ * it, not to the system).  This returns the pool's unused blocks on the
+ * current device to the system.  Memory in use, and memory whose stream-ordered
+ * free has not run yet, stays.  Not in the paper.
+ * Errors: SN_ECUDA.
+ */
+sn_status sn_trim_memory(void);
+
+/*
  * z-slab decomposition (Sec. 4.2 and 5: regions are left open at the volume's
  * faces, so sub-volumes can be processed apart and their meshes joined).  A
  * rank extracts and smooths a slab of sample slices with ghost slices on both

@@ -145,7 +145,8 @@ sn_status pool_alloc(void **p, size_t bytes, cudaMemPool_t pool, cudaStream_t st
 
 void pool_free(void *p, cudaStream_t st)
 {
-    if (p) cudaFreeAsync(p, st);
+    // (a failed free must not leave its error for the next launch to report)
+    if (p && cudaFreeAsync(p, st) != cudaSuccess) cudaGetLastError();
 }
 
 // Pinned host block for the count read-back, one per thread.
@@ -535,9 +536,9 @@ sn_status job_count(ExtractJob &j, cudaStream_t st, bool shared_totals = false)
     return SN_OK;
 }
 
-// Exact allocation of the outputs from the totals (end of Pass 3), in one
-// block; with_smooth_buffer also places the smoothing buffer there.
-sn_status job_allocate(ExtractJob &j, cudaStream_t st, bool with_smooth_buffer = false)
+// The mesh of a job from its totals (end of Pass 3): counts, record mode and
+// cell-code layout, no device memory yet.
+sn_status job_mesh(ExtractJob &j, cudaStream_t st)
 {
     const sn::DevTotals *htot = j.htot;
     if (htot->error)
@@ -562,7 +563,6 @@ sn_status job_allocate(ExtractJob &j, cudaStream_t st, bool with_smooth_buffer =
     m->nq = nq;
     m->ns = ns;
     m->a.rec = sn::rec_mode(*htot, &m->a.by, &m->a.bz);
-    const int64_t nx = j.dims[0], ny = j.dims[1], nz = j.dims[2];
     {
         // cell codes in 32 bits when the three extents (cell coordinate + 1 in [0, n]) fit
         auto bits = [](int64_t v) {
@@ -570,50 +570,74 @@ sn_status job_allocate(ExtractJob &j, cudaStream_t st, bool with_smooth_buffer =
             while ((1ll << b) <= v) ++b;
             return b;
         };
-        const int bx = bits(nx), byy = bits(ny), bzz = bits(nz);
+        const int bx = bits(j.dims[0]), byy = bits(j.dims[1]), bzz = bits(j.dims[2]);
         m->a.cell_wide = bx + byy + bzz > 32;
         m->a.cell_sy = m->a.cell_wide ? 21 : bx;
         m->a.cell_sz = m->a.cell_wide ? 42 : bx + byy;
     }
-    struct {
-        void **p;
-        size_t bytes;
-        const char *what;
-    } oplan[] = {
-        {(void **)&m->a.points, sizeof(float) * 3 * (size_t)np, "points"},
-        {(void **)&m->a.offsets, sizeof(float) * 3 * (size_t)np, "offsets"},
-        {(void **)&m->a.cells, (m->a.cell_wide ? sizeof(uint64_t) : sizeof(uint32_t)) * (size_t)np, "cells"},
-        {(void **)&m->a.quads, sizeof(int32_t) * 4 * (size_t)nq, "quads"},
-        {(void **)&m->a.quad_labels, (size_t)j.type * 2 * (size_t)nq, "quad labels"},
-        {(void **)&m->a.sten_off, sizeof(int64_t) * (size_t)(np + 1), "stencil offsets"},
-        {(void **)&m->a.sten_ids, sizeof(int32_t) * (size_t)ns, "stencil ids"},
-        {(void **)&m->a.face_mask, (size_t)np, "face masks"},
-        {(void **)&m->a.meta, sizeof(int32_t) * 4, "mesh meta"},
-        {(void **)&m->a.nbr, sizeof(uint2) * (size_t)np, "smoothing neighbours"},
-        {(void **)&m->a.nbrp, m->a.rec == sn::REC_WIDE ? sizeof(uint32_t) * (size_t)np : 0, "smoothing neighbours"},
-        {(void **)&m->a.lut_x, sizeof(float2) * (size_t)(nx + ny + nz + 3), "cell-centre tables"},
-    };
-    // one block for all outputs (+ the smoothing buffer when asked), each array on a 256-byte boundary
-    const size_t smooth_bytes = with_smooth_buffer ? sizeof(float) * 3 * (size_t)np : 0;
-    size_t total = (smooth_bytes + 255) / 256 * 256;
-    for (auto &pl : oplan) total += (pl.bytes + 255) / 256 * 256;
-    sn_status r = pool_alloc((void **)&m->arena, total, j.pool, st, "mesh outputs");
-    if (r != SN_OK) {
+    j.mesh = m;
+    return SN_OK;
+}
+
+// Calls f(pointer slot, bytes) for each output array of a mesh, in arena order.
+template <typename F> void mesh_arrays(sn_mesh *m, F &&f)
+{
+    const size_t np = (size_t)m->np, nq = (size_t)m->nq, ns = (size_t)m->ns;
+    f((void **)&m->a.points, sizeof(float) * 3 * np);
+    f((void **)&m->a.offsets, sizeof(float) * 3 * np);
+    f((void **)&m->a.cells, (m->a.cell_wide ? sizeof(uint64_t) : sizeof(uint32_t)) * np);
+    f((void **)&m->a.quads, sizeof(int32_t) * 4 * nq);
+    f((void **)&m->a.quad_labels, (size_t)m->type * 2 * nq);
+    f((void **)&m->a.sten_off, sizeof(int64_t) * (np + 1));
+    f((void **)&m->a.sten_ids, sizeof(int32_t) * ns);
+    f((void **)&m->a.face_mask, np);
+    f((void **)&m->a.meta, sizeof(int32_t) * 4);
+    f((void **)&m->a.nbr, sizeof(uint2) * np);
+    f((void **)&m->a.nbrp, m->a.rec == sn::REC_WIDE ? sizeof(uint32_t) * np : 0);
+    f((void **)&m->a.lut_x, sizeof(float2) * (size_t)(m->dims[0] + m->dims[1] + m->dims[2] + 3));
+}
+
+// Bytes of a mesh's arena: every output array (+ the smoothing buffer when
+// asked), each on a 256-byte boundary.
+size_t mesh_arena_bytes(sn_mesh *m, bool with_smooth_buffer)
+{
+    size_t total = with_smooth_buffer ? (sizeof(float) * 3 * (size_t)m->np + 255) / 256 * 256 : 0;
+    mesh_arrays(m, [&](void **, size_t bytes) { total += (bytes + 255) / 256 * 256; });
+    return total;
+}
+
+// Places a mesh's arrays in `block` (mesh_arena_bytes of it).
+void mesh_place(sn_mesh *m, char *block, size_t bytes, bool with_smooth_buffer)
+{
+    m->arena = block;
+    m->arena_bytes = bytes;
+    char *at = block;
+    mesh_arrays(m, [&](void **p, size_t n) {
+        *p = at;
+        at += (n + 255) / 256 * 256;
+    });
+    if (with_smooth_buffer && m->np > 0) m->smooth_scratch = reinterpret_cast<float *>(at); // (an empty buffer has no place)
+    if (m->a.rec != sn::REC_WIDE) m->a.nbrp = nullptr; // (given no bytes above)
+    m->centres_pending = true;
+    m->a.lut_y = m->a.lut_x + (m->dims[0] + 1);
+    m->a.lut_z = m->a.lut_y + (m->dims[1] + 1);
+}
+
+// Exact allocation of the outputs from the totals (end of Pass 3), in one
+// block; with_smooth_buffer also places the smoothing buffer there.
+sn_status job_allocate(ExtractJob &j, cudaStream_t st, bool with_smooth_buffer = false)
+{
+    sn_status r = job_mesh(j, st);
+    if (r != SN_OK) return r;
+    sn_mesh *m = j.mesh;
+    const size_t total = mesh_arena_bytes(m, with_smooth_buffer);
+    char *block = nullptr;
+    if ((r = pool_alloc((void **)&block, total, j.pool, st, "mesh outputs")) != SN_OK) {
+        j.mesh = nullptr;
         sn_free(m);
         return r;
     }
-    m->arena_bytes = total;
-    char *block = m->arena;
-    for (auto &pl : oplan) {
-        *pl.p = block;
-        block += (pl.bytes + 255) / 256 * 256;
-    }
-    if (smooth_bytes) m->smooth_scratch = reinterpret_cast<float *>(block);
-    if (m->a.rec != sn::REC_WIDE) m->a.nbrp = nullptr; // (given no bytes above)
-    m->centres_pending = true;
-    m->a.lut_y = m->a.lut_x + (nx + 1);
-    m->a.lut_z = m->a.lut_y + (ny + 1);
-    j.mesh = m;
+    mesh_place(m, block, total, with_smooth_buffer);
     return SN_OK;
 }
 
@@ -662,6 +686,18 @@ void job_release(ExtractJob &j, cudaStream_t st)
 extern "C" {
 
 void sn_profile_enable(int on) { g_prof_on.store(on ? 1 : 0); }
+
+sn_status sn_trim_memory(void)
+{
+    g_last_error.clear();
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    cudaMemPool_t pool = nullptr;
+    if ((e = device_pool(dev, &pool)) != cudaSuccess) return cuda_fail(e, "memory pool");
+    if ((e = cudaMemPoolTrimTo(pool, 0)) != cudaSuccess) return cuda_fail(e, "pool trim");
+    return SN_OK;
+}
 
 void sn_debug_set_spin_limit(int limit) { g_spin_limit.store(limit); }
 

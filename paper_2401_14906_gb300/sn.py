@@ -85,6 +85,7 @@ SIGNATURES = {
     "sn_learn_gradient": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
     "sn_learner_step": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float]),
     "sn_profile_enable": (None, [ctypes.c_int]),
+    "sn_trim_memory": (ctypes.c_int, []),
     "sn_profile_read": (ctypes.c_int, [ctypes.POINTER(sn_kernel_time), ctypes.c_int, ctypes.c_int]),
     "sn_slab_part_of": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                        ctypes.POINTER(sn_slab_part)]),
@@ -404,6 +405,11 @@ def sn_smooth_static(stencil_offsets, stencil_ids, face_masks, n_points, iterati
 
 def sn_profile_enable(on=True):
     load().sn_profile_enable(1 if on else 0)
+
+
+def sn_trim_memory():
+    """Return the library's unused pooled device memory on the current device to the system."""
+    _check(load().sn_trim_memory())
 
 
 def sn_profile_read(reset=False):

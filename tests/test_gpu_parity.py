@@ -7,6 +7,7 @@ every label width, selected-label modes and the degenerate cases.
 import numpy as np
 import pytest
 
+import oracle
 import sn_synth
 from gpu_util import parity
 
@@ -241,6 +242,24 @@ def test_triangulation_smoothed():
     parity(w.labels, iterations=16, triangulate=TRI)
     lab = sn_synth.atlas((96, 80, 72), n_seeds=12, seed=14)
     parity(lab, spacing=(1.0, 1.0, 2.0), iterations=9, sphere=True, triangulate=TRI)
+
+
+def test_trim_memory_between_calls():
+    """sn_trim_memory returns the pool's unused blocks; meshes alive across it keep their memory, and the next
+    extraction allocates afresh."""
+    import torch
+    from paper_2401_14906_gb300 import sn
+    lab = sn_synth.ellipsoids((60, 50, 40), 5, 3.0, 12.0, np.uint16, seed=9)
+    t = torch.from_numpy(lab.view(np.int16)).cuda().view(torch.uint16)
+    keep = sn.sn_extract(t)
+    sn.sn_extract(t).free()
+    torch.cuda.synchronize()
+    sn.sn_trim_memory()
+    got = sn.sn_mesh_copy_to_host(keep)
+    keep.free()
+    ref = oracle.extract(lab)
+    np.testing.assert_array_equal(got["quads"], ref.quads)
+    parity(lab, iterations=4)
 
 
 def test_determinism():
