@@ -1743,7 +1743,7 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
         std::vector<int64_t> two_kernel;
         // the batched counting launches of all maps with one tile shape (tables freed with the jobs)
         auto count_all = [&](const CountShape &shape, bool record_two_kernel) -> sn_status {
-            CountGroup groups[3][2];
+            CountGroup groups[3][3]; // [label type][counting form]
             for (int64_t i = 0; i < n_maps; ++i) {
                 ExtractJob &j = jobs[i];
                 sn::CountTiling tl;
@@ -1752,7 +1752,7 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
                 bool batched = j.cls.mode == sn::CLASS_ALL &&
                                sn::count_tiling(j.type, j.dlabels, j.g, &tl, &smem, shape.slot_kb, shape.min_kz);
                 if (batched) {
-                    CountGroup &G = groups[ti][tl.aligned ? 1 : 0];
+                    CountGroup &G = groups[ti][tl.realign ? 2 : tl.aligned ? 1 : 0];
                     sn::CountBatchMap d;
                     std::memset(&d, 0, sizeof(d));
                     d.lab = j.dlabels;
@@ -1774,9 +1774,9 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
                 if (!batched && record_two_kernel) two_kernel.push_back(i);
             }
             DeviceTables tabs;
-            size_t at[3][2][2] = {};
+            size_t at[3][3][2] = {};
             for (int ti = 0; ti < 3; ++ti)
-                for (int f = 0; f < 2; ++f)
+                for (int f = 0; f < 3; ++f)
                     if (!groups[ti][f].maps.empty()) {
                         at[ti][f][0] = tabs.add(groups[ti][f].maps);
                         at[ti][f][1] = tabs.add(groups[ti][f].start);
@@ -1786,11 +1786,11 @@ sn_status sn_extract_smooth_batch(int64_t n_maps, const void *const *labels, con
             if (r != SN_OK) return r;
             jobs[0].temps.push_back(dt);
             for (int ti = 0; ti < 3; ++ti)
-                for (int f = 0; f < 2; ++f) {
+                for (int f = 0; f < 3; ++f) {
                     const CountGroup &G = groups[ti][f];
                     if (G.maps.empty()) continue;
                     const cudaError_t e2 = sn::launch_count_batch(
-                        kTypes[ti], f == 1, reinterpret_cast<const sn::CountBatchMap *>(dt + at[ti][f][0]),
+                        kTypes[ti], f, reinterpret_cast<const sn::CountBatchMap *>(dt + at[ti][f][0]),
                         reinterpret_cast<const uint32_t *>(dt + at[ti][f][1]), (int)G.maps.size(), (uint32_t)G.blocks,
                         G.smem, st);
                     if (e2 != cudaSuccess) return cuda_fail(e2, "batched counting launch");

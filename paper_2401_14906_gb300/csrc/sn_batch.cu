@@ -35,7 +35,7 @@ constexpr int kBatchCountThreads = SN_COUNT_THREADS;
 constexpr int kBatchEmitThreads = SN_EMIT_THREADS;
 constexpr int kMaxOptinSmem = 227 * 1024; // dynamic shared memory a CTA may opt in to
 
-template <typename T, bool FAST>
+template <typename T, int FORM>
 __global__ void __launch_bounds__(kBatchCountThreads, SN_BATCH_COUNT_MINBLOCKS)
     k_count_batch(const CountBatchMap *__restrict__ maps, const uint32_t *__restrict__ block_start, int n,
                   uint32_t desc_at)
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kBatchCountThreads, SN_BATCH_COUNT_MINBLOCKS)
     const int i = find_map_cta(block_start, n, b, map_sh);
     load_map(mp, maps + i);
     const int64_t local = (int64_t)(b - block_start[i]);
-    count_tile<T, CLASS_ALL, FAST>(reinterpret_cast<const T *>(mp->lab), mp->c, mp->g, mp->s, mp->tl, mp->tot,
+    count_tile<T, CLASS_ALL, FORM>(reinterpret_cast<const T *>(mp->lab), mp->c, mp->g, mp->s, mp->tl, mp->tot,
                                    local % mp->gx, mp->tl.zt0 + local / mp->gx);
 }
 
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kBatchEmitThreads, 6)
 // that the tiles' dynamic shared memory starts where their own launches have it)
 inline uint32_t desc_offset(size_t tile_smem) { return (uint32_t)((tile_smem + 15) / 16 * 16); }
 
-template <typename T, bool FAST>
+template <typename T, int FORM>
 cudaError_t count_batch_t(const CountBatchMap *maps, const uint32_t *start, int n, uint32_t blocks, size_t tile_smem,
                           cudaStream_t st)
 {
@@ -96,9 +96,9 @@ cudaError_t count_batch_t(const CountBatchMap *maps, const uint32_t *start, int 
     const size_t smem = at + sizeof(CountBatchMap) + 16;
     if (smem > (size_t)kMaxOptinSmem) return cudaErrorInvalidValue;
     static std::atomic<uint64_t> done{0};
-    cudaError_t e = smem_limit_once(k_count_batch<T, FAST>, kMaxOptinSmem, done);
+    cudaError_t e = smem_limit_once(k_count_batch<T, FORM>, kMaxOptinSmem, done);
     if (e != cudaSuccess) return e;
-    k_count_batch<T, FAST><<<blocks, kBatchCountThreads, smem, st>>>(maps, start, n, at);
+    k_count_batch<T, FORM><<<blocks, kBatchCountThreads, smem, st>>>(maps, start, n, at);
     return cudaGetLastError();
 }
 
@@ -116,21 +116,25 @@ cudaError_t emit_batch_t(const EmitBatchMap *maps, const uint32_t *start, int n,
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t count_batch_f(int form, const CountBatchMap *maps, const uint32_t *start, int n, uint32_t blocks,
+                          size_t tile_smem, cudaStream_t st)
+{
+    if (form == FORM_STAGED) return count_batch_t<T, FORM_STAGED>(maps, start, n, blocks, tile_smem, st);
+    if (form == FORM_DIRECT) return count_batch_t<T, FORM_DIRECT>(maps, start, n, blocks, tile_smem, st);
+    return count_batch_t<T, FORM_SCALAR>(maps, start, n, blocks, tile_smem, st);
+}
+
 } // namespace
 
-cudaError_t launch_count_batch(int type, bool fast, const CountBatchMap *maps, const uint32_t *block_start, int n,
+cudaError_t launch_count_batch(int type, int form, const CountBatchMap *maps, const uint32_t *block_start, int n,
                                uint32_t blocks, size_t tile_smem, cudaStream_t st)
 {
     if (n <= 0 || blocks == 0) return cudaSuccess;
     ProfScope ps("k_count_batch", st);
-    if (type == SN_U8)
-        return fast ? count_batch_t<uint8_t, true>(maps, block_start, n, blocks, tile_smem, st)
-                    : count_batch_t<uint8_t, false>(maps, block_start, n, blocks, tile_smem, st);
-    if (type == SN_U16)
-        return fast ? count_batch_t<uint16_t, true>(maps, block_start, n, blocks, tile_smem, st)
-                    : count_batch_t<uint16_t, false>(maps, block_start, n, blocks, tile_smem, st);
-    return fast ? count_batch_t<uint32_t, true>(maps, block_start, n, blocks, tile_smem, st)
-                : count_batch_t<uint32_t, false>(maps, block_start, n, blocks, tile_smem, st);
+    if (type == SN_U8) return count_batch_f<uint8_t>(form, maps, block_start, n, blocks, tile_smem, st);
+    if (type == SN_U16) return count_batch_f<uint16_t>(form, maps, block_start, n, blocks, tile_smem, st);
+    return count_batch_f<uint32_t>(form, maps, block_start, n, blocks, tile_smem, st);
 }
 
 cudaError_t launch_scan_batch(const ScanBatchMap *maps, const uint32_t *block_start, int n, uint32_t blocks,

@@ -206,13 +206,20 @@ __device__ __forceinline__ void edge_words(const Classifier &c, const T *row, co
     }
 }
 
+// How a counting tile gets its label rows (CountTiling): element by element with
+// per-sample compares, by bulk copies of rows on 16-byte boundaries, or by bulk
+// copies of the aligned span around the slice block moved to a 16-byte pitch.
+// A compile-time choice, so that each form carries only its own code.
+enum CountForm { FORM_SCALAR = 0, FORM_DIRECT = 1, FORM_STAGED = 2 };
+
 // One tile (bx, by) of the counting pass.  Label rows are g.lp elements apart.  Returns false (in every
 // thread) when a label copy wait gave up; the copy may then still be in flight.
-template <typename T, int MODE, bool FAST>
+template <typename T, int MODE, int FORM>
 __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Classifier &c, const Geometry &g,
                                            const ExtractScratch &s, const CountTiling &tl, DevTotals *tot, int64_t bx,
                                            int64_t by)
 {
+    constexpr bool FAST = FORM != FORM_SCALAR; // packed compares of 16-byte chunks in shared memory
     extern __shared__ __align__(128) uint8_t smem[];
     const int TY = tl.ty, W = tl.W, tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
     const int64_t nx = g.nx, ny = g.ny, nz = g.nz, lp = g.lp;
@@ -239,14 +246,16 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
         const int slot = (int)((kk - k0) % kCountSlots);
         const T *src = lab + (kk * ny + j0) * lp;
         T *dst = reinterpret_cast<T *>(slots + (size_t)slot * tl.slot_bytes);
-        if (tl.aligned) {
+        if (FORM != FORM_SCALAR) {
             if (tid == 0) {
                 // realign: the 16-byte aligned span around the slice block, to the staging area
                 const uintptr_t a = reinterpret_cast<uintptr_t>(src);
-                const uintptr_t a0 = tl.realign ? a & ~(uintptr_t)15 : a;
-                const uint32_t bytes = tl.realign ? (uint32_t)(((a + slice_bytes + 15) & ~(uintptr_t)15) - a0)
-                                                  : slice_bytes;
-                void *to = tl.realign ? (void *)(slots + (size_t)slot * tl.slot_bytes + tl.stage_off) : (void *)dst;
+                const uintptr_t a0 = FORM == FORM_STAGED ? a & ~(uintptr_t)15 : a;
+                const uint32_t bytes = FORM == FORM_STAGED
+                                           ? (uint32_t)(((a + slice_bytes + 15) & ~(uintptr_t)15) - a0)
+                                           : slice_bytes;
+                void *to = FORM == FORM_STAGED ? (void *)(slots + (size_t)slot * tl.slot_bytes + tl.stage_off)
+                                               : (void *)dst;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_expect_tx(&bars[slot], bytes);
                 bulk_load(to, reinterpret_cast<const void *>(a0), bytes, &bars[slot]);
@@ -286,7 +295,7 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
     for (int e = tid; e < 2 * plane_words; e += nthr) planes[e] = 0u;
     __syncthreads();
     for (int q = 0; q < kCountSlots; ++q) issue(k0 + q);
-    if (!tl.aligned) __syncthreads();
+    if (FORM == FORM_SCALAR) __syncthreads();
 
     uint32_t phase_bits = 0; // parity of the next completion of each slot
     bool failed = false;
@@ -311,7 +320,7 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
         const bool have_next = kk + 1 < k_ld_end && kk < k_own_end;
         int32_t *cb = cnt + (int)((kk - k0) & 1) * cstride;       // this step's counters
         const int32_t *cbp = cnt + (int)((kk - k0 + 1) & 1) * cstride; // the previous step's
-        if (tl.aligned && tid == 0) { // one thread waits; the barrier below releases the others
+        if (FORM != FORM_SCALAR && tid == 0) { // one thread waits; the barrier below releases the others
             for (int d = 0; d < 2; ++d) {
                 const int64_t kq = kk + d;
                 if ((d == 0 && !have) || (d == 1 && !have_next)) continue;
@@ -322,7 +331,7 @@ __device__ __forceinline__ bool count_tile(const T *__restrict__ lab, const Clas
                 }
             }
         }
-        if (tl.realign) {
+        if (FORM == FORM_STAGED) {
             __syncthreads(); // thread 0 has seen the staged slices land
             if (kk == k0 && have) realign_slice(kk);
             if (have_next) realign_slice(kk + 1);

@@ -138,11 +138,11 @@ __global__ void __launch_bounds__(256) k_cellrows(Geometry g, ExtractScratch s)
 #endif
 constexpr int kCountThreads = SN_COUNT_THREADS;
 
-template <typename T, int MODE, bool FAST>
-__global__ void __launch_bounds__(kCountThreads, SN_COUNT_MINBLOCKS) k_count(const T *__restrict__ lab, Classifier c, Geometry g, ExtractScratch s,
-                                               CountTiling tl, DevTotals *tot)
+template <typename T, int MODE, int FORM>
+__global__ void __launch_bounds__(kCountThreads, SN_COUNT_MINBLOCKS)
+    k_count(const T *__restrict__ lab, Classifier c, Geometry g, ExtractScratch s, CountTiling tl, DevTotals *tot)
 {
-    count_tile<T, MODE, FAST>(lab, c, g, s, tl, tot, blockIdx.x, tl.zt0 + (int64_t)blockIdx.y);
+    count_tile<T, MODE, FORM>(lab, c, g, s, tl, tot, blockIdx.x, tl.zt0 + (int64_t)blockIdx.y);
 }
 
 // Single-map scan: tiles are numbered by a ticket in the order blocks start.
@@ -419,7 +419,7 @@ cudaError_t emit_m(int type, const void *labels, const Classifier &c, const Geom
 
 constexpr size_t kCountMaxSmem = 200 * 1024;
 
-template <typename T, int MODE, bool FAST>
+template <typename T, int MODE, int FORM>
 cudaError_t count_f(const void *labels, const Classifier &c, const Geometry &g, const ExtractScratch &s,
                     const CountTiling &tl, size_t smem, DevTotals *tot, cudaStream_t st)
 {
@@ -427,11 +427,11 @@ cudaError_t count_f(const void *labels, const Classifier &c, const Geometry &g, 
     // launches captured into one graph with different tilings all stay within it
     if (smem > kCountMaxSmem) return cudaErrorInvalidValue;
     static std::atomic<uint64_t> done{0};
-    cudaError_t e = smem_limit_once(k_count<T, MODE, FAST>, (int)kCountMaxSmem, done);
+    cudaError_t e = smem_limit_once(k_count<T, MODE, FORM>, (int)kCountMaxSmem, done);
     if (e != cudaSuccess) return e;
     if (tl.zt1 <= tl.zt0) return cudaSuccess;
     dim3 grid((unsigned)((g.ny + tl.ty - 1) / tl.ty), (unsigned)(tl.zt1 - tl.zt0));
-    k_count<T, MODE, FAST><<<grid, kCountThreads, smem, st>>>((const T *)labels, c, g, s, tl, tot);
+    k_count<T, MODE, FORM><<<grid, kCountThreads, smem, st>>>((const T *)labels, c, g, s, tl, tot);
     return cudaGetLastError();
 }
 
@@ -439,9 +439,10 @@ template <typename T, int MODE>
 cudaError_t count_t(const void *labels, const Classifier &c, const Geometry &g, const ExtractScratch &s,
                     const CountTiling &tl, size_t smem, DevTotals *tot, cudaStream_t st)
 {
-    // packed compares need rows on 16-byte boundaries (labels are classified in shared memory first)
-    if (tl.aligned) return count_f<T, MODE, true>(labels, c, g, s, tl, smem, tot, st);
-    return count_f<T, MODE, false>(labels, c, g, s, tl, smem, tot, st);
+    // packed compares need rows on 16-byte boundaries in shared memory: copied so (direct) or moved so (staged)
+    if (tl.realign) return count_f<T, MODE, FORM_STAGED>(labels, c, g, s, tl, smem, tot, st);
+    if (tl.aligned) return count_f<T, MODE, FORM_DIRECT>(labels, c, g, s, tl, smem, tot, st);
+    return count_f<T, MODE, FORM_SCALAR>(labels, c, g, s, tl, smem, tot, st);
 }
 
 template <int MODE>

@@ -223,8 +223,8 @@ struct EmitBatchMap {
     TileGeom tg;
     int64_t gx; // tiles of a slice (the single-map grid's x extent)
 };
-// fast: every map's rows start on 16-byte boundaries (CountTiling::aligned)
-cudaError_t launch_count_batch(int type, bool fast, const CountBatchMap *maps, const uint32_t *block_start, int n,
+// form: how every map's tiles get their rows (dev::CountForm: 0 element-wise, 1 direct, 2 staged)
+cudaError_t launch_count_batch(int type, int form, const CountBatchMap *maps, const uint32_t *block_start, int n,
                                uint32_t blocks, size_t tile_smem, cudaStream_t st);
 cudaError_t launch_scan_batch(const ScanBatchMap *maps, const uint32_t *block_start, int n, uint32_t blocks,
                               cudaStream_t st);
