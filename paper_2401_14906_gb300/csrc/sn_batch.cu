@@ -3,11 +3,11 @@
 // the GPU's CTAs instead of each launching its own grid).
 //
 // Every CTA first finds its map among the per-map block offsets, copies that
-// map's descriptor (geometry, scratch, outputs, tiling)
-// into shared memory, and then runs the same tile function the single-map
-// kernel runs, with the block index relative to its map.  The descriptor sits
-// after the largest tile's shared memory of the launch, so the tile functions
-// see their own layout unchanged.
+// map's descriptor (geometry, scratch, outputs, tiling) into shared memory, and
+// then runs the same tile function the single-map kernel runs, with the block
+// index relative to its map.  The descriptor sits after the largest tile's
+// shared memory of the launch, so the tile functions see their own layout
+// unchanged.
 #include "sn_count.cuh"
 #include "sn_emit_tile.cuh"
 #include "sn_scan.cuh"
@@ -15,9 +15,7 @@
 #ifndef SN_COUNT_THREADS
 #define SN_COUNT_THREADS 256
 #endif
-#ifndef SN_COUNT_MINBLOCKS
-#define SN_COUNT_MINBLOCKS 2
-#endif
+// resident counting tiles per SM the registers are sized for: four (the batch's maps are small, its slots 16 KB)
 #ifndef SN_BATCH_COUNT_MINBLOCKS
 #define SN_BATCH_COUNT_MINBLOCKS 4
 #endif
