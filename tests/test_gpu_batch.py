@@ -168,6 +168,31 @@ def test_batch_of_every_counting_and_emission_form(graph, tune):
         compare_smooth(got, off_ref, pts_ref, (1.0, 1.0, 1.0), 1.0)
 
 
+def test_batch_of_degenerate_shapes():
+    """Extents of 1 along each axis and along all three, with every label type, in one batch: the batched counting,
+    scan and emission tiles at their smallest (one row, one slice, one word), against the oracle."""
+    sn = _sn()
+    rng = np.random.default_rng(123)
+    shapes = [(1, 1, 1), (1, 7, 1), (9, 1, 1), (1, 1, 12), (3, 2, 1), (1, 5, 6), (33, 1, 4), (2, 40, 1)]
+    maps = []
+    for n, (nz, ny, nx) in enumerate(shapes):
+        dt = (np.uint8, np.uint16, np.uint32)[n % 3]
+        maps.append(rng.integers(0, 3, size=(nz, ny, nx)).astype(dt))
+    meshes = sn.sn_extract_smooth_batch([_dev(m) for m in maps], iterations=3, relaxation=0.5,
+                                        constraint_distance=1.0)
+    for lab, m in zip(maps, meshes):
+        got = _host(m)
+        m.free()
+        ref = oracle.extract(lab)
+        assert got["points"].shape[0] == ref.n_points and got["quads"].shape[0] == ref.n_quads
+        for k, want in (("quads", ref.quads), ("quad_labels", ref.quad_labels), ("face_masks", ref.face_masks),
+                        ("stencil_offsets", ref.stencil_offsets), ("stencil_ids", ref.stencil_ids)):
+            np.testing.assert_array_equal(got[k], want, err_msg=k)
+        if ref.n_points:
+            off_ref, pts_ref = oracle.smooth(ref, iterations=3, relaxation=0.5, constraint=1.0)
+            compare_smooth(got, off_ref, pts_ref, (1.0, 1.0, 1.0), 1.0)
+
+
 def test_degenerate_batches():
     sn = _sn()
     assert sn.sn_extract_smooth_batch([]) == []
