@@ -29,6 +29,7 @@ namespace {
 using namespace dev;
 
 constexpr int kEmitThreads = SN_EMIT_THREADS;
+constexpr int kEmitMaxSmem = 227 * 1024; // dynamic shared memory a CTA may opt in to
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kEmitThreads) k_emit_tile(const T *__restrict__ lab, Classifier c, Geometry g,
@@ -41,13 +42,11 @@ template <typename T, int MODE>
 cudaError_t emit_tile_t(const void *labels, const Classifier &c, const Geometry &g, const ExtractScratch &s,
                         const MeshArrays &m, DevTotals *tot, const TileGeom &tg, size_t smem, cudaStream_t st)
 {
-    // one fixed limit (the largest tile any launch may use), so that launches captured
-    // into one graph with different tile shapes all stay within it
-    static const int kMaxSmem =
-        (int)(sizeof(uint32_t) * (size_t)TileSmem(kEmitMaxRows, kTileMaxW, kTileMaxW, kListCapMax).total);
-    if (smem > (size_t)kMaxSmem) return cudaErrorInvalidValue;
+    // one fixed limit (the most a CTA may opt in to), so that launches captured into one
+    // graph with different tile shapes all stay within it; emit_tiling keeps tiles below it
+    if (smem > (size_t)kEmitMaxSmem) return cudaErrorInvalidValue;
     static std::atomic<uint64_t> done{0};
-    cudaError_t e = smem_limit_once(k_emit_tile<T, MODE>, kMaxSmem, done);
+    cudaError_t e = smem_limit_once(k_emit_tile<T, MODE>, kEmitMaxSmem, done);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((g.ny + 1 + tg.ty - 1) / tg.ty), (unsigned)(g.nz + 1));
     k_emit_tile<T, MODE><<<grid, kEmitThreads, smem, st>>>((const T *)labels, c, g, s, m, tot, tg);
@@ -67,7 +66,9 @@ cudaError_t emit_tile_m(int type, const void *labels, const Classifier &c, const
 // Default cell rows per tile: the most (at most kEmitMaxRows, in steps of 4)
 // whose shared memory lets five tiles of kEmitThreads threads stay resident per
 // SM (228 KB per SM, 1 KB of it reserved per CTA).  Dense maps (many points per
-// row) gain from the residency; sparse ones from the longer tiles.
+// row) gain from the residency; sparse and narrow ones from the taller tiles,
+// which spread the tile's fixed work (staging, per-word prefixes, barriers)
+// over more rows.
 int default_rows(int W, int WS, int lcap)
 {
 #ifdef SN_EMIT_ROWS_FIXED
@@ -96,7 +97,7 @@ bool emit_tiling(const Geometry &g, int rows, int64_t items, TileGeom *out, size
     tg.wdiv = (0x100000000ull + (uint64_t)g.W - 1) / (uint64_t)g.W;
     *out = tg;
     *smem = sizeof(uint32_t) * (size_t)TileSmem(tg.ty, tg.W, tg.WS, tg.lcap).total;
-    return true;
+    return *smem <= (size_t)kEmitMaxSmem; // (else the per-row kernels)
 }
 
 cudaError_t launch_emit_tile(int type, const void *labels, const Classifier &c, const Geometry &g,

@@ -132,7 +132,7 @@ struct TileGeom {
     int lcap;      // entries of the position list (points or quads listed per chunk)
 };
 
-constexpr int kEmitMaxRows = 32;
+constexpr int kEmitMaxRows = 128; // the point list's entries carry the tile row in 7 bits
 
 // Sets a kernel's dynamic shared-memory limit once per device (`done` is a
 // per-kernel bit set of the devices already done).
